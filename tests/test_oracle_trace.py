@@ -1,0 +1,197 @@
+"""Pins of the oracle's traversal, attenuation, splitting and whole-field results (Sec. 2.1).
+
+Each test compares against something other than the oracle's own formulas: brute-force
+dense sampling of the ray, hand-computed visit sequences, exact geometric exit lengths,
+exact photon bookkeeping, the paper's split radius and ray counts, and the r^-2 vacuum law
+with the accuracy the paper reports.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")))
+
+
+def _prob(n, nH0=None, pos=((0.5, 0.5, 0.5),), L=(1.0,), **kw):
+    if nH0 is None:
+        nH0 = np.zeros((n, n, n))
+    return O.Problem(nH0=nH0, pos=np.asarray(pos, float), L=np.asarray(L, float), dx=1.0 / n, **kw)
+
+
+def _exit_length(u, v, n):
+    """Distance (cell units) from u along unit v to the box [0, n]^3."""
+    t = math.inf
+    for a in range(3):
+        if v[a] > 0:
+            t = min(t, (n - u[a]) / v[a])
+        elif v[a] < 0:
+            t = min(t, -u[a] / v[a])
+    return t
+
+
+def _brute(u, v, n, tmax, samples):
+    """Per-cell path lengths by dense midpoint sampling of x = u + t v, t in [0, tmax]."""
+    dt = tmax / samples
+    t = (np.arange(samples) + 0.5) * dt
+    p = u[None, :] + t[:, None] * v[None, :]
+    c = np.floor(p).astype(np.int64)
+    inside = np.all((c >= 0) & (c < n), axis=1)
+    idx = c[inside, 0] + n * (c[inside, 1] + n * c[inside, 2])
+    cells, counts = np.unique(idx, return_counts=True)
+    return dict(zip(cells.tolist(), (counts * dt).tolist()))
+
+
+def test_brute_force_path_lengths():
+    rng = np.random.default_rng(11)
+    n = 8
+    for trial in range(12):
+        u = rng.uniform(0.5, n - 0.5, 3)
+        R = np.linalg.qr(rng.standard_normal((3, 3)))[0]
+        if np.linalg.det(R) < 0:
+            R[:, 0] *= -1
+        level = 2
+        pix = int(rng.integers(0, 12 * 4**level))
+        prob = _prob(n, pos=[u / n], level0=level, level_cap=level, rot=R)
+        cells, ds, end = O.ray_segments(prob, level, pix)
+        assert end == 0
+        v = R @ O.pix2vec(level, pix)
+        texit = _exit_length(u, v, n)
+        got = {}
+        for c, d in zip(cells.tolist(), ds.tolist()):
+            got[c] = got.get(c, 0.0) + d * n
+        assert sum(got.values()) == pytest.approx(texit, abs=1e-12)
+        ref = _brute(u, v, n, texit, 2_000_000)
+        assert set(ref) <= set(got)
+        for c, d in got.items():
+            assert abs(d - ref.get(c, 0.0)) < 1.5e-5, (trial, c)
+
+
+def test_axis_ray_visit_sequence():
+    n = 8
+    prob = _prob(n, pos=[[3.5 / n] * 3], level0=0, level_cap=0)
+    cells, ds, end = O.ray_segments(prob, 0, 4)  # level-0 pixel 4 is +x
+    exp_cells = [i + n * (3 + n * 3) for i in range(3, 8)]
+    assert cells.tolist() == exp_cells
+    assert np.allclose(ds * n, [0.5, 1, 1, 1, 1], atol=1e-15)
+    assert end == 0
+
+
+def test_diagonal_ray_steps_both_axes():
+    n = 8
+    c = s = math.sqrt(0.5)
+    R = np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])  # +x -> (1,1,0)/sqrt2
+    prob = _prob(n, pos=[[3.5 / n] * 3], level0=0, level_cap=0, rot=R)
+    cells, ds, end = O.ray_segments(prob, 0, 4)
+    exp_cells = [k + n * (k + n * 3) for k in range(3, 8)]
+    assert cells.tolist() == exp_cells
+    assert np.allclose(ds * n, np.array([0.5, 1, 1, 1, 1]) * math.sqrt(2), atol=1e-14)
+
+
+def test_corner_source_face_rules():
+    n = 8
+    prob = _prob(n, pos=[[4.0 / n] * 3], level0=0, level_cap=0)
+    cells, ds, _ = O.ray_segments(prob, 0, 4)   # +x along an edge: upper cells in y and z
+    assert cells.tolist() == [i + n * (4 + n * 4) for i in range(4, 8)]
+    cells, ds, _ = O.ray_segments(prob, 0, 6)   # -x: the lower cell in x
+    assert cells.tolist() == [i + n * (4 + n * 4) for i in range(3, -1, -1)]
+    assert np.allclose(ds * n, 1.0)
+
+
+def test_split_radius_matches_paper():
+    g = GOLD["split_radius"]
+    n = 64
+    prob = _prob(n, pos=[[0.5 + 0.3 / n, 0.5 + 0.1 / n, 0.5 - 0.2 / n]], level0=4, m_ray=g["m_ray"])
+    for pix in (0, 777, 3071):
+        cells, ds, end = O.ray_segments(prob, 4, pix)
+        assert end == 2
+        assert ds.sum() * n == pytest.approx(g["r_max_over_dx_level4"], rel=1e-9)
+
+
+def test_uniform_medium_absorption_closed_form():
+    n = 8
+    chi = 5.5  # per unit length (0.6875 per cell), exact in float32
+    rng = np.random.default_rng(3)
+    u = rng.uniform(1.0, 7.0, 3)
+    prob = _prob(n, nH0=np.full((n, n, n), chi), pos=[u / n], L=[2.0], level0=1, level_cap=1,
+                 sigma_H=1.0)
+    r = O.trace(prob)
+    want = 0.0
+    path = 0.0
+    for p in range(48):
+        s = _exit_length(u, O.pix2vec(1, p), n) / n
+        want += 2.0 / 48 * (1 - math.exp(-chi * s))
+        path += s
+    assert r.absorbed == pytest.approx(want, rel=1e-12)
+    assert float((chi * r.G).sum()) == pytest.approx(want, rel=1e-12)
+    assert r.escaped == pytest.approx(2.0 - want, rel=1e-12)
+    assert r.dropped == 0.0
+
+
+def test_vacuum_path_sum_rule():
+    n = 12
+    rng = np.random.default_rng(5)
+    u = rng.uniform(1.0, 11.0, 3)
+    prob = _prob(n, pos=[u / n], L=[3.0], level0=2, level_cap=2)
+    r = O.trace(prob)
+    path = sum(_exit_length(u, O.pix2vec(2, p), n) / n for p in range(192))
+    assert float(r.G.sum()) == pytest.approx(3.0 / 192 * path, rel=1e-12)
+    assert r.absorbed == 0.0 and r.escaped == pytest.approx(3.0, rel=1e-15)
+
+
+def test_photon_conservation_and_destroy_counter():
+    from paper_1711_06277_gb300 import synth
+    n = 24
+    rho = synth.lognormal_field(n, 1.5, seed=2).astype(np.float32).astype(np.float64)
+    pos = synth.uniform_positions(5, seed=4)
+    L = synth.power_law_luminosities(5, seed=4)
+    prob = _prob(n, nH0=rho, pos=pos, L=L, sigma_H=12.0, level0=2, tau_max=8.0)
+    r = O.trace(prob)
+    assert r.absorbed + r.escaped + r.dropped == pytest.approx(r.L_in, rel=1e-12)
+    assert float((12.0 * rho * r.G).sum()) == pytest.approx(r.absorbed, rel=1e-10)
+    assert r.destroy == r.destroy_expected == 5 * 12 * 4**r.level_max
+    assert r.dropped <= math.exp(-8.0) * r.L_in
+    assert r.dropped > 0
+
+
+def test_rays_per_level_exact_in_vacuum():
+    n = 64
+    prob = _prob(n, pos=[[0.5, 0.5, 0.5]], level0=4)
+    r = O.trace(prob)
+    # r_max(4), r_max(5), r_max(6) = 7.8, 15.6, 31.3 cells are all inside the 32-cell
+    # half-width, so every ray splits at those levels; level 7 (r_max 62.5) reaches the
+    # farthest corner (55.4) and never splits.
+    assert r.level_max == 7
+    assert r.rays_per_level[4:9].tolist() == [3072, 12288, 49152, 196608, 0]
+    assert r.destroy == 12 * 4**7
+
+
+def test_level_max_rule():
+    n = 32
+    r = O.trace(_prob(n, nH0=np.ones((n, n, n)), sigma_H=5.0))
+    assert r.level_max == 6            # r_max(6) = 31.3 >= sqrt(3) * 16 = 27.7 > r_max(5)
+    assert r.rays_per_level[4:8].tolist() == [3072, 12288, 49152, 0]
+    assert r.near_tie_rays == 0
+
+
+@pytest.mark.slow
+def test_vacuum_inverse_square_accuracy():
+    g = GOLD["vacuum"]
+    n = 128
+    prob = _prob(n, pos=[[0.5, 0.5, 0.5]], level0=4, m_ray=4.0)
+    r = O.trace(prob, nthreads=4)
+    c = np.arange(n) + 0.5
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    rr = np.sqrt((x - 64) ** 2 + (y - 64) ** 2 + (z - 64) ** 2)
+    sel = (rr > 4) & (rr < 60)
+    exact = 1.0 / (4 * np.pi * (rr[sel] / n) ** 2)
+    err4 = np.abs(r.energy[sel] / exact - 1)
+    lo, hi = g["median_rel_err_m4_l4_range"]
+    assert lo <= np.median(err4) <= hi
+    r16 = O.trace(_prob(n, pos=[[0.5, 0.5, 0.5]], level0=4, m_ray=16.0), nthreads=4)
+    err16 = np.abs(r16.energy[sel] / exact - 1)
+    assert np.median(err16) < 0.5 * np.median(err4)
