@@ -1,0 +1,353 @@
+"""Benchmark of the adaptive ray trace on one GB300 (and N independent replicas under
+torchrun).
+
+Workload (default): the coupled trace + ionization-balance step on a 512^3 lognormal grid
+(sigma_ln = 2.0, k^-4 power spectrum, mean n_H = 100 in code units) with 1024 power-law
+sources: one step = one batched persistent trace of all sources + the Eq. e:xn3 update of the
+neutral fraction, whose result feeds the next step's neutral density. Metric: cell-segment
+crossings per second. Inputs (512 MB density, 2 GB accumulator) exceed the 129 MB L2, so no
+L2 flush is needed between steps.
+
+Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1711_06277_gb300 import synth  # noqa: E402
+
+BYTES_PER_CROSSING = 20  # 4 B opacity gather + 16 B deposit reduction
+
+CONFIGS = {
+    # name: (n, sigma_ln, nsrc, seed)
+    "c5_512_1024src": dict(n=512, sigma_ln=2.0, nsrc=1024, seed=5, nbar=100.0, sigma_H=0.1,
+                           alpha=2e-4, x0=1e-3),
+    "c3_256_64src": dict(n=256, sigma_ln=2.0, nsrc=64, seed=3, nbar=1.0, sigma_H=10.0,
+                         alpha=None, x0=1.0),
+}
+
+
+def _measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([v.strip() for v in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for k, v in zip(names, s[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(k)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.samples)}
+
+
+def make_workload(cfg: dict, rank: int = 0):
+    n = cfg["n"]
+    seed = cfg["seed"] + 1000 * rank
+    rho = synth.lognormal_field(n, cfg["sigma_ln"], seed=seed)
+    nH = (cfg["nbar"] * rho).astype(np.float32)
+    pos = synth.uniform_positions(cfg["nsrc"], seed=seed)
+    L = synth.power_law_luminosities(cfg["nsrc"], seed=seed)
+    return nH, pos, L
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1711_06277_gb300 import art as A
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    cfg = CONFIGS[args.config]
+    n = cfg["n"]
+    nH_h, pos, L = make_workload(cfg, rank)
+    x0 = cfg["x0"]
+    nH = torch.from_numpy(nH_h).to(dev)
+    xn = torch.full_like(nH, x0)
+    nH0 = (xn * nH).contiguous()
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        grid = A.Grid(nH0, 1.0 / n, stream=stream)
+        grid.add_sources(pos, L)
+    p = A.Params(level0=4, m_ray=4.0, tau_max=30.0, sigma_H=cfg["sigma_H"],
+                 schedule=args.schedule, chunk=args.chunk, block_threads=args.block_threads)
+    gamma = torch.empty_like(nH)
+    alpha = cfg["alpha"]
+    dt = 0.1 / (alpha * cfg["nbar"]) if alpha else 0.0
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def step(timed_trace=None):
+        with torch.cuda.stream(stream):
+            if timed_trace is not None:
+                timed_trace[0].record(stream)
+            out = grid.trace(p, force=False, stats=True, out={"gamma": gamma})
+            if timed_trace is not None:
+                timed_trace[1].record(stream)
+            if alpha:
+                A.xn_update(gamma, nH, xn, alpha, dt, nH0_out=nH0, stream=stream)
+        return out["stats"]
+
+    for _ in range(args.warmup):
+        step()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    cross = 0
+    trace_ms = []
+    tev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with ClockSampler(local_rank) as clk:
+        ev[0].record(stream)
+        for _ in range(args.steps):
+            st = step(tev)
+            cross += st["crossings"]
+            trace_ms.append(tev[0].elapsed_time(tev[1]))
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    ms = ev[0].elapsed_time(ev[1])
+    tot = torch.tensor([ms, float(cross)], dtype=torch.float64, device=dev)
+    if world > 1:
+        mx = tot.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tot.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms_all, cross_all = float(mx[0]), float(sm[1])
+    else:
+        ms_all, cross_all = ms, float(cross)
+    value = cross_all / (ms_all / 1e3)
+
+    # dominant kernel: the persistent trace (its API call, incl. the small set-up kernels)
+    peak, peak_kind = _measured_peaks()
+    trace_s = statistics.mean(trace_ms) / 1e3
+    per_launch_cross = cross / args.steps
+    achieved = per_launch_cross * BYTES_PER_CROSSING / trace_s / 1e9
+
+    # end to end through the public API with host buffers (pinned): H2D of the neutral
+    # density, trace + update, D2H of the updated neutral fraction
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.empty(nH0.shape, dtype=torch.float32, pin_memory=True)
+        h_in.copy_(nH0.cpu())
+        h_out = torch.empty_like(h_in, pin_memory=True)
+        e_cross = 0
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e_steps = max(1, min(args.steps, 3))
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(e_steps):
+                nH0.copy_(h_in, non_blocking=True)
+                st = step()
+                h_out.copy_(xn, non_blocking=True)
+                e_cross += st["crossings"]
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e_ms = e0.elapsed_time(e1)
+        nbytes = nH0.numel() * 4
+        e2e = {"value": e_cross / (e_ms / 1e3), "unit": "crossings/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": e_steps}
+
+    extra = {}
+    if args.compare_plain and rank == 0:
+        extra["plain_vs_persistent"] = compare_schedules(A, dev)
+    grid.close()
+    return {
+        "value": value, "ms": ms_all, "cross": cross_all, "clocks": clk.summary(),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "k_trace_persistent (art_trace call)",
+                     "bytes_per_crossing": BYTES_PER_CROSSING,
+                     "crossings_per_launch": per_launch_cross,
+                     "launch_ms": trace_s * 1e3},
+        "e2e": e2e, "extra": extra,
+    }
+
+
+def compare_schedules(A, dev):
+    """Persistent batched trace vs the plain one-source-per-launch trace, 256^3 / 64 sources."""
+    import torch
+    cfg = CONFIGS["c3_256_64src"]
+    nH_h, pos, L = make_workload(cfg)
+    nH0 = torch.from_numpy(nH_h).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    g = A.Grid(nH0, 1.0 / cfg["n"], stream=stream)
+    g.add_sources(pos, L)
+    res = {}
+    for sched in ("persistent", "plain"):
+        p = A.Params(level0=4, tau_max=30.0, sigma_H=cfg["sigma_H"], schedule=sched)
+        g.trace(p, force=False)
+        torch.cuda.synchronize(dev)
+        t = []
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = g.trace(p, force=False)["stats"]
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            t.append(e0.elapsed_time(e1))
+        res[sched] = {"ms": min(t), "crossings": st["crossings"],
+                      "crossings_per_s": st["crossings"] / (min(t) / 1e3)}
+    res["speedup"] = res["plain"]["ms"] / res["persistent"]["ms"]
+    g.close()
+    return res
+
+
+def run_reference(args):
+    """FP64 CPU oracle on a bounded sample: one source of the workload per step."""
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    cfg = CONFIGS[args.config]
+    n = cfg["n"]
+    nH_h, pos, L = make_workload(cfg)
+    nH0 = (cfg["x0"] * nH_h.astype(np.float64)).astype(np.float32)
+    threads = os.cpu_count() or 1
+
+    def one(k):
+        s = k % len(L)
+        prob = O.Problem(nH0=nH0, pos=pos[s:s + 1], L=L[s:s + 1], dx=1.0 / n,
+                         sigma_H=cfg["sigma_H"], level0=4, m_ray=4.0, tau_max=30.0)
+        return O.trace(prob, nthreads=threads).crossings
+
+    for k in range(args.warmup):
+        one(k)
+    t0 = time.perf_counter()
+    cross = 0
+    for k in range(args.steps):
+        cross += one(args.warmup + k)
+    dt = time.perf_counter() - t0
+    value = cross / dt
+    sample = (f"one source per step (sources {args.warmup}..{args.warmup + args.steps - 1}) of "
+              f"the {n}^3 / {cfg['nsrc']}-source workload at its initial neutral fraction")
+    return {"value": value, "ms": dt * 1e3 / args.steps, "threads": threads, "sample": sample}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c5_512_1024src", choices=sorted(CONFIGS))
+    ap.add_argument("--schedule", default="persistent", choices=["persistent", "plain"])
+    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--block-threads", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--compare-plain", action="store_true", default=True)
+    ap.add_argument("--no-compare-plain", dest="compare_plain", action="store_false")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    cfg = CONFIGS[args.config]
+    config = {"workload": f"{cfg['n']}^3 lognormal sigma_ln={cfg['sigma_ln']}, {cfg['nsrc']} "
+                          f"power-law sources, l0=4, m_ray=4, tau_max=30"
+                          + (", trace + Eq. e:xn3 update per step" if cfg["alpha"] else ""),
+              "grid": cfg["n"], "sources": cfg["nsrc"], "schedule": args.schedule,
+              "l2": "inputs larger than L2 (512 MB density, 2 GB accumulator)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        r = run_reference(args)
+        line = {"impl": "reference", "metric": "cell-segment crossings/s", "value": r["value"],
+                "unit": "crossings/s", "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config,
+                "cpu_baseline": {"value": r["value"], "unit": "crossings/s", "cores": r["threads"],
+                                 "kind": "oracle", "sample": r["sample"]},
+                "e2e": {"value": r["value"], "unit": "crossings/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    r = run_ours(args, rank, world, local_rank)
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        ra = argparse.Namespace(**{**vars(args), "steps": 1, "warmup": 0})
+        rr = run_reference(ra)
+        cpu = {"value": rr["value"], "unit": "crossings/s", "cores": rr["threads"],
+               "kind": "oracle", "sample": rr["sample"]}
+    line = {"metric": "cell-segment crossings/s", "value": r["value"], "unit": "crossings/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+            "clocks": r["clocks"], "roofline": r["roofline"], "cpu_baseline": cpu,
+            "e2e": r["e2e"], "gpu_launches": 5 * args.steps}
+    line.update(r["extra"])
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

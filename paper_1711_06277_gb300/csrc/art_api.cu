@@ -1,0 +1,485 @@
+// art_api.cu -- C ABI of the GB300 adaptive ray trace: grid object, argument checks,
+// buffer management and the launch sequences of the forward trace.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "art.h"
+#include "art_kernels.cuh"
+#include "art_internal.h"
+
+using namespace art;
+
+namespace {
+
+constexpr double kDefaultWaitS = 10.0;
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return ART_OK;
+    if (e == cudaErrorMemoryAllocation) return ART_ENOMEM;
+    return ART_ECUDA;
+}
+
+#define ART_TRY(expr)                     \
+    do {                                  \
+        int _rc = cuda_status(expr);      \
+        if (_rc != ART_OK) return _rc;    \
+    } while (0)
+
+double rmax_unit(double m_ray) { return std::sqrt(3.0 / (M_PI * m_ray)); }
+
+// l_max of a source at u (cell units): smallest l >= l0 whose split radius reaches the
+// farthest corner of the box, capped at ART_MAX_LEVEL; or the fixed cap.
+int source_level_max(const art_grid* g, const double u[3], int level0, int cap, double m_ray)
+{
+    if (cap >= 0) return cap;
+    double far2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double e = std::fmax(u[a], (double)g->n[a] - u[a]);
+        far2 += e * e;
+    }
+    const double far = std::sqrt(far2);
+    const double unit = rmax_unit(m_ray);
+    int l = level0;
+    while (l < ART_MAX_LEVEL && unit * std::ldexp(1.0, l) < far) ++l;
+    return l;
+}
+
+void split_df(double v, float& hi, float& lo)
+{
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+template <class T>
+int dev_alloc(T** p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cuda_status(cudaMalloc((void**)p, count * sizeof(T)));
+}
+
+void dev_free(void* p)
+{
+    if (p) cudaFree(p);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// shared helpers (declared in art_internal.h)
+// ---------------------------------------------------------------------------------------
+namespace art {
+
+int check_params(const art_params* p)
+{
+    if (!p) return ART_EINVAL;
+    if (p->level0 < 0 || p->level0 > 8) return ART_EINVAL;
+    if (p->level_max >= 0 && (p->level_max < p->level0 || p->level_max > ART_MAX_LEVEL))
+        return ART_EINVAL;
+    if (!(p->m_ray > 0.0) || !std::isfinite(p->m_ray)) return ART_EINVAL;
+    if (!(p->tau_max > 0.0) || !(p->tau_max < 3.0e38)) return ART_EINVAL;
+    if (!(p->sigma_H >= 0.0) || !(p->sigma_d >= 0.0) || !std::isfinite(p->sigma_H) ||
+        !std::isfinite(p->sigma_d))
+        return ART_EINVAL;
+    if (p->schedule != ART_SCHED_PERSISTENT && p->schedule != ART_SCHED_PLAIN) return ART_EINVAL;
+    if (p->block_threads != 0 &&
+        (p->block_threads % 32 != 0 || p->block_threads < 64 || p->block_threads > 1024))
+        return ART_EINVAL;
+    if (p->chunk != 0 && (p->chunk < 32 || p->chunk % 32 != 0)) return ART_EINVAL;
+    if (p->queue_capacity != 0 && p->queue_capacity < 4) return ART_EINVAL;
+    if (p->flags & ART_F_ROTATE)
+        for (int i = 0; i < 9; ++i)
+            if (!std::isfinite(p->rot[i])) return ART_EINVAL;
+    return ART_OK;
+}
+
+// Source table, per-source l_max, direction tables, level constants and ray buffers for a
+// trace with parameters p. Allocates only when something grew or changed.
+int prepare_trace(art_grid* g, const art_params* p, bool adjoint)
+{
+    const int ns = (int)g->L.size();
+    if (ns == 0) return ART_ESTATE;
+    const int l0 = p->level0;
+    const unsigned npix0 = 12u << (2 * l0);
+    // --- sources: cell-unit positions as df, base-ray luminosity, l_max
+    std::vector<SrcDev> hs(ns);
+    int lmax_glob = l0;
+    g->src_lmax.resize(ns);
+    for (int s = 0; s < ns; ++s) {
+        double u[3];
+        for (int a = 0; a < 3; ++a) u[a] = (g->pos[3 * s + a] - g->lo[a]) / g->dx;
+        int lm = source_level_max(g, u, l0, p->level_max, p->m_ray);
+        g->src_lmax[s] = lm;
+        if (lm > lmax_glob) lmax_glob = lm;
+        float h[3], lo[3];
+        for (int a = 0; a < 3; ++a) split_df(u[a], h[a], lo[a]);
+        const double lb = adjoint ? 1.0 / (double)npix0 : g->L[s] / (double)npix0;
+        int lmi = lm;
+        float lmf;
+        std::memcpy(&lmf, &lmi, sizeof(float));
+        hs[s].hi = make_float4(h[0], h[1], h[2], (float)lb);
+        hs[s].lo = make_float4(lo[0], lo[1], lo[2], lmf);
+    }
+    if ((size_t)ns > g->src_cap) {
+        dev_free(g->d_src);
+        g->d_src = nullptr;
+        g->src_cap = 0;
+        int rc = dev_alloc(&g->d_src, ns);
+        if (rc) return rc;
+        g->src_cap = ns;
+    }
+    ART_TRY(cudaMemcpyAsync(g->d_src, hs.data(), ns * sizeof(SrcDev), cudaMemcpyHostToDevice,
+                            g->stream));
+    g->lmax_glob = lmax_glob;
+    // --- direction tables (FP64 HEALPix, rotated), rebuilt when the rotation changes
+    const bool rotate = (p->flags & ART_F_ROTATE) != 0;
+    bool same_rot = g->dir_rotate == rotate;
+    if (rotate && same_rot)
+        for (int i = 0; i < 9; ++i) same_rot = same_rot && g->dir_rot[i] == p->rot[i];
+    if (!same_rot) {
+        for (int l = 0; l < kNL; ++l) g->dir_built[l] = false;
+        g->dir_rotate = rotate;
+        for (int i = 0; i < 9; ++i) g->dir_rot[i] = rotate ? p->rot[i] : (i % 4 == 0 ? 1.0 : 0.0);
+    }
+    for (int l = l0; l <= lmax_glob; ++l) {
+        const unsigned long long npix = 12ull << (2 * l);
+        if (!g->dir_hi[l]) {
+            int rc = dev_alloc(&g->dir_hi[l], npix);
+            if (!rc) rc = dev_alloc(&g->dir_lo[l], npix);
+            if (rc) return rc;
+            g->dir_built[l] = false;
+        }
+        if (!g->dir_built[l]) {
+            const double* r = g->dir_rot;
+            unsigned blocks = (unsigned)((npix + 255) / 256);
+            k_directions<<<blocks, 256, 0, g->stream>>>(l, npix, r[0], r[1], r[2], r[3], r[4],
+                                                        r[5], r[6], r[7], r[8], rotate ? 1 : 0,
+                                                        g->dir_hi[l], g->dir_lo[l]);
+            ART_TRY(cudaGetLastError());
+            g->dir_built[l] = true;
+        }
+    }
+    // --- level constants
+    LevelInfo lv[kNL];
+    std::memset(lv, 0, sizeof(lv));
+    const double unit = rmax_unit(p->m_ray);
+    for (int l = l0; l <= lmax_glob; ++l) {
+        double r0 = l > l0 ? unit * std::ldexp(1.0, l - 1) : 0.0;
+        double r1 = unit * std::ldexp(1.0, l);
+        split_df(r0, lv[l].r0.hi, lv[l].r0.lo);
+        split_df(r1, lv[l].rmax.hi, lv[l].rmax.lo);
+        lv[l].dir_hi = g->dir_hi[l];
+        lv[l].dir_lo = g->dir_lo[l];
+        lv[l].destroy_w = 1ull << (2 * (lmax_glob - l));
+    }
+    ART_TRY(cudaMemcpyAsync(g->d_levels, lv, sizeof(lv), cudaMemcpyHostToDevice, g->stream));
+    // --- ray buffers: level l0 holds every base ray of the batch; deeper levels hold at
+    // most the queue capacity (persistent) or one source's whole front (plain)
+    const bool plain = p->schedule == ART_SCHED_PLAIN;
+    long long qcap = p->queue_capacity > 0 ? p->queue_capacity : (64ll << 20);
+    for (int l = l0; l <= lmax_glob; ++l) {
+        unsigned long long need;
+        const unsigned long long front = 12ull << (2 * l);  // rays of one source at level l
+        if (l == l0) need = plain ? npix0 : (unsigned long long)ns * npix0;
+        else if (plain) need = p->queue_capacity > 0 ? (unsigned long long)qcap : front;
+        else need = std::min<unsigned long long>((unsigned long long)qcap, (unsigned long long)ns * front);
+        need = (need + 3) & ~3ull;
+        const bool want_adj = adjoint && !g->buf_adj[l];
+        if (need > g->buf_cap[l] || want_adj) {
+            RayBuf& b = g->buf[l];
+            dev_free(b.src); dev_free(b.pix); dev_free(b.L); dev_free(b.tau);
+            dev_free(b.parent); dev_free(b.own); dev_free(b.sub);
+            b = RayBuf{};
+            g->buf_cap[l] = 0;
+            const unsigned long long cap = std::max(need, g->buf_cap_req[l]);
+            int rc = dev_alloc(&b.src, cap);
+            if (!rc) rc = dev_alloc(&b.pix, cap);
+            if (!rc) rc = dev_alloc(&b.L, cap);
+            if (!rc) rc = dev_alloc(&b.tau, cap);
+            if (!rc && (adjoint || g->buf_adj[l])) {
+                rc = dev_alloc(&b.parent, cap);
+                if (!rc) rc = dev_alloc(&b.own, cap);
+                if (!rc) rc = dev_alloc(&b.sub, cap);
+                g->buf_adj[l] = true;
+            }
+            if (rc) return rc;
+            g->buf_cap[l] = cap;
+            g->buf_cap_req[l] = cap;
+        }
+        g->buf[l].cap = need;  // the capacity this trace may use
+    }
+    for (int l = lmax_glob + 1; l < kNL; ++l) {
+        RayBuf keep = g->buf[l];
+        keep.cap = 0;
+        g->buf[l] = keep;
+    }
+    // --- opacity per cell length
+    const double sH_dx = p->sigma_H * g->dx;
+    const double sd_dx = g->nH ? p->sigma_d * g->dx : 0.0;
+    int blocks = (int)std::min<long long>((g->ncell + 255) / 256, (long long)g->sms * 16);
+    k_opacity<<<blocks, 256, 0, g->stream>>>(g->ncell, g->nH0, g->nH, sH_dx, sd_dx, g->d_chi,
+                                             adjoint ? g->d_chiH : nullptr, g->d_stats);
+    ART_TRY(cudaGetLastError());
+    return ART_OK;
+}
+
+TraceArgs make_args(art_grid* g, const art_params* p)
+{
+    TraceArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.nx = g->n[0];
+    A.ny = g->n[1];
+    A.nz = g->n[2];
+    A.level0 = p->level0;
+    A.lmax_glob = g->lmax_glob;
+    A.chunk = p->chunk > 0 ? p->chunk : 64;
+    A.tau_max = (float)p->tau_max;
+    A.chi = g->d_chi;
+    A.chiH = g->d_chiH;
+    A.acc = g->d_acc;
+    A.src = g->d_src;
+    A.levels = g->d_levels;
+    for (int l = 0; l < kNL; ++l) A.buf[l] = g->buf[l];
+    A.sched = g->d_sched;
+    A.stats = g->d_stats;
+    double ws = p->wait_limit_s == 0.0 ? kDefaultWaitS : p->wait_limit_s;
+    A.wait_ns = ws < 0.0 ? -1 : (long long)(ws * 1e9);
+    return A;
+}
+
+int finish_stats(art_grid* g, art_stats* out)
+{
+    ART_TRY(cudaStreamSynchronize(g->stream));
+    const DevStats& d = *g->h_stats;
+    std::memset(out, 0, sizeof(*out));
+    out->crossings = d.crossings;
+    out->rays_total = d.rays_total;
+    for (int l = 0; l < ART_NLEVELS && l < kNL; ++l) out->rays_per_level[l] = d.rays_per_level[l];
+    out->destroy = d.destroy;
+    out->destroy_expected = g->destroy_expected;
+    out->L_in = g->last_L_in;
+    out->L_absorbed = d.absorbed;
+    out->L_escaped = d.escaped;
+    out->L_dropped = d.dropped;
+    out->level_reached = d.level_reached;
+    out->level_max = g->last_lmax;
+    int st = ART_OK;
+    if (d.error == -1) st = ART_EINVAL;
+    else if (d.error < 0) st = d.error;
+    else if (g->last_kind == 0 && d.destroy != g->destroy_expected) st = ART_EACCOUNTING;
+    out->status = st;
+    return st;
+}
+
+}  // namespace art
+
+// ---------------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------------
+extern "C" {
+
+void art_params_default(art_params* p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->level0 = 4;
+    p->level_max = -1;
+    p->m_ray = 4.0;
+    p->tau_max = 7.0;
+    p->sigma_H = 1.0;
+    p->sigma_d = 0.0;
+    p->rot[0] = p->rot[4] = p->rot[8] = 1.0;
+    p->flags = 0;
+    p->schedule = ART_SCHED_PERSISTENT;
+}
+
+int art_create_grid(art_grid** out, int nx, int ny, int nz, const double box_lo[3], double dx,
+                    const float* d_nH0, const float* d_nH, void* stream)
+{
+    if (!out) return ART_EINVAL;
+    *out = nullptr;
+    if (nx <= 0 || ny <= 0 || nz <= 0 || !box_lo || !(dx > 0.0) || !std::isfinite(dx) || !d_nH0)
+        return ART_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(box_lo[a])) return ART_EINVAL;
+    const long long ncell = (long long)nx * ny * nz;
+    if (ncell >= (1ll << 31)) return ART_EINVAL;
+    art_grid* g = new (std::nothrow) art_grid();
+    if (!g) return ART_ENOMEM;
+    g->n[0] = nx; g->n[1] = ny; g->n[2] = nz;
+    g->ncell = ncell;
+    for (int a = 0; a < 3; ++a) g->lo[a] = box_lo[a];
+    g->dx = dx;
+    g->nH0 = d_nH0;
+    g->nH = d_nH;
+    g->stream = (cudaStream_t)stream;
+    int rc = cuda_status(cudaGetDevice(&g->device));
+    if (!rc) rc = cuda_status(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device));
+    if (!rc) rc = dev_alloc(&g->d_chi, ncell);
+    if (!rc) rc = dev_alloc(&g->d_acc, ncell);
+    if (!rc) rc = dev_alloc(&g->d_levels, kNL);
+    if (!rc) rc = dev_alloc(&g->d_sched, 1);
+    if (!rc) rc = dev_alloc(&g->d_stats, 1);
+    if (!rc) rc = cuda_status(cudaMallocHost((void**)&g->h_stats, sizeof(DevStats)));
+    if (rc) {
+        art_destroy_grid(g);
+        return rc;
+    }
+    std::memset(g->h_stats, 0, sizeof(DevStats));
+    *out = g;
+    return ART_OK;
+}
+
+int art_update_fields(art_grid* g, const float* d_nH0, const float* d_nH)
+{
+    if (!g || !d_nH0) return ART_EINVAL;
+    g->nH0 = d_nH0;
+    g->nH = d_nH;
+    return ART_OK;
+}
+
+int art_add_sources(art_grid* g, int n, const double* h_pos, const double* h_L)
+{
+    if (!g || n < 0 || (n > 0 && (!h_pos || !h_L))) return ART_EINVAL;
+    for (int s = 0; s < n; ++s) {
+        if (!(h_L[s] >= 0.0) || !std::isfinite(h_L[s])) return ART_EINVAL;
+        for (int a = 0; a < 3; ++a) {
+            double u = (h_pos[3 * s + a] - g->lo[a]) / g->dx;
+            if (!(u > 0.0 && u < (double)g->n[a])) return ART_EINVAL;
+        }
+    }
+    g->pos.insert(g->pos.end(), h_pos, h_pos + 3 * (size_t)n);
+    g->L.insert(g->L.end(), h_L, h_L + (size_t)n);
+    return ART_OK;
+}
+
+int art_clear_sources(art_grid* g)
+{
+    if (!g) return ART_EINVAL;
+    g->pos.clear();
+    g->L.clear();
+    return ART_OK;
+}
+
+int art_num_sources(const art_grid* g) { return g ? (int)g->L.size() : 0; }
+
+int art_trace(art_grid* g, const art_params* p, float* d_gamma, float* d_force, float* d_energy,
+              art_stats* h_stats)
+{
+    if (!g || !d_gamma) return ART_EINVAL;
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (g->L.empty()) return ART_ESTATE;
+    ART_TRY(cudaMemsetAsync(g->d_stats, 0, sizeof(DevStats), g->stream));
+    rc = prepare_trace(g, p, false);
+    if (rc) return rc;
+    ART_TRY(cudaMemsetAsync(g->d_acc, 0, sizeof(float4) * (size_t)g->ncell, g->stream));
+    ART_TRY(cudaMemsetAsync(g->d_sched, 0, sizeof(Sched), g->stream));
+    const int ns = (int)g->L.size();
+    const int l0 = p->level0;
+    const unsigned npix0 = 12u << (2 * l0);
+    const int threads = p->block_threads > 0 ? p->block_threads : 256;
+    TraceArgs A = make_args(g, p);
+    if (p->schedule == ART_SCHED_PLAIN) {
+        int per_sm = 0;
+        ART_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_level, threads, 0));
+        if (per_sm < 1) return ART_EINVAL;
+        const int grid = per_sm * g->sms;
+        for (int s = 0; s < ns; ++s) {
+            k_reset_counts<<<1, 32, 0, g->stream>>>(g->d_sched);
+            k_inject<<<(npix0 + 255) / 256, 256, 0, g->stream>>>(s, 1, npix0, g->buf[l0],
+                                                                  &g->d_sched->count[l0]);
+            for (int l = l0; l <= g->src_lmax[s]; ++l)
+                k_trace_level<<<grid, threads, 0, g->stream>>>(A, l);
+        }
+        ART_TRY(cudaGetLastError());
+    } else {
+        unsigned long long nb = (unsigned long long)ns * npix0;
+        k_inject<<<(unsigned)((nb + 255) / 256), 256, 0, g->stream>>>(0, ns, npix0, g->buf[l0],
+                                                                     &g->d_sched->count[l0]);
+        ART_TRY(cudaGetLastError());
+        int per_sm = 0;
+        ART_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent, threads, 0));
+        if (per_sm < 1) return ART_EINVAL;
+        cudaLaunchConfig_t cfg;
+        std::memset(&cfg, 0, sizeof(cfg));
+        cfg.gridDim = dim3(per_sm * g->sms);
+        cfg.blockDim = dim3(threads);
+        cfg.stream = g->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        ART_TRY(cudaLaunchKernelEx(&cfg, k_trace_persistent, A));
+    }
+    const double dV = g->dx * g->dx * g->dx;
+    const float gscale = (float)(p->sigma_H * g->dx / dV);
+    const float fscale = (float)(1.0 / dV);
+    const float escale = (float)(g->dx / dV);
+    int blocks = (int)std::min<long long>((g->ncell + 255) / 256, (long long)g->sms * 16);
+    k_finalize<<<blocks, 256, 0, g->stream>>>(g->ncell, g->d_acc, gscale, fscale, escale,
+                                              d_gamma, d_force, d_energy);
+    ART_TRY(cudaGetLastError());
+    ART_TRY(cudaMemcpyAsync(g->h_stats, g->d_stats, sizeof(DevStats), cudaMemcpyDeviceToHost,
+                            g->stream));
+    double Lin = 0.0;
+    for (double v : g->L) Lin += v;
+    g->last_L_in = Lin;
+    g->last_lmax = g->lmax_glob;
+    g->destroy_expected = (unsigned long long)ns * (12ull << (2 * g->lmax_glob));
+    g->last_kind = 0;
+    g->traced = true;
+    if (h_stats) return finish_stats(g, h_stats);
+    return ART_OK;
+}
+
+int art_get_stats(art_grid* g, art_stats* h_stats)
+{
+    if (!g || !h_stats) return ART_EINVAL;
+    if (!g->traced) return ART_ESTATE;
+    return finish_stats(g, h_stats);
+}
+
+void art_destroy_grid(art_grid* g)
+{
+    if (!g) return;
+    if (g->stream || true) cudaStreamSynchronize(g->stream);
+    dev_free(g->d_chi);
+    dev_free(g->d_chiH);
+    dev_free(g->d_acc);
+    dev_free(g->d_src);
+    dev_free(g->d_levels);
+    dev_free(g->d_sched);
+    dev_free(g->d_stats);
+    for (int l = 0; l < kNL; ++l) {
+        dev_free(g->dir_hi[l]);
+        dev_free(g->dir_lo[l]);
+        RayBuf& b = g->buf[l];
+        dev_free(b.src); dev_free(b.pix); dev_free(b.L); dev_free(b.tau);
+        dev_free(b.parent); dev_free(b.own); dev_free(b.sub);
+    }
+    if (g->h_stats) cudaFreeHost(g->h_stats);
+    delete g;
+}
+
+const char* art_strerror(int status)
+{
+    switch (status) {
+    case ART_OK: return "ok";
+    case ART_EINVAL: return "invalid argument or input value";
+    case ART_ENOMEM: return "out of device or pinned host memory";
+    case ART_EQUEUE_OVERFLOW: return "a ray front exceeded its buffer capacity";
+    case ART_ETIMEOUT: return "a bounded device-side wait ran out";
+    case ART_EACCOUNTING: return "retired-ray weights do not add up to N_src*12*4^l_max";
+    case ART_ECUDA: return "CUDA runtime error";
+    case ART_ESTATE: return "call out of order (no sources or nothing traced)";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

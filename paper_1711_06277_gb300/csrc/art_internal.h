@@ -1,0 +1,62 @@
+// art_internal.h -- host-side grid object shared by the translation units of the library.
+#pragma once
+
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "art.h"
+#include "art_device.cuh"
+
+struct art_grid {
+    int device = 0;
+    int sms = 1;
+    cudaStream_t stream = nullptr;
+    int n[3] = {0, 0, 0};
+    long long ncell = 0;
+    double lo[3] = {0, 0, 0};
+    double dx = 1.0;
+    const float* nH0 = nullptr;  // borrowed
+    const float* nH = nullptr;   // borrowed, may be NULL
+    std::vector<double> pos, L;  // host copies of the sources
+    std::vector<int> src_lmax;
+
+    // device buffers owned by the grid
+    float* d_chi = nullptr;      // opacity per cell length
+    float* d_chiH = nullptr;     // its neutral-H part (adjoint)
+    float4* d_acc = nullptr;     // per-cell accumulator
+    art::SrcDev* d_src = nullptr;
+    size_t src_cap = 0;
+    art::LevelInfo* d_levels = nullptr;
+    art::Sched* d_sched = nullptr;
+    art::DevStats* d_stats = nullptr;
+    art::DevStats* h_stats = nullptr;  // pinned
+
+    float4* dir_hi[art::kNL] = {};
+    float4* dir_lo[art::kNL] = {};
+    bool dir_built[art::kNL] = {};
+    bool dir_rotate = false;
+    double dir_rot[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+
+    art::RayBuf buf[art::kNL] = {};
+    unsigned long long buf_cap[art::kNL] = {};      // allocated rays per level
+    unsigned long long buf_cap_req[art::kNL] = {};
+    bool buf_adj[art::kNL] = {};                     // adjoint arrays allocated
+
+    // adjoint scratch
+    float* d_tmp_grad = nullptr;
+
+    int lmax_glob = 0;
+    int last_lmax = 0;
+    int last_kind = 0;  // 0 forward, 1 backward
+    double last_L_in = 0.0;
+    unsigned long long destroy_expected = 0;
+    bool traced = false;
+};
+
+namespace art {
+int check_params(const art_params* p);
+int prepare_trace(art_grid* g, const art_params* p, bool adjoint);
+TraceArgs make_args(art_grid* g, const art_params* p);
+int finish_stats(art_grid* g, art_stats* out);
+}  // namespace art

@@ -1,0 +1,427 @@
+// art_kernels.cuh -- forward trace kernels of the GB300 adaptive ray trace.
+//
+// Work decomposition. The rays of one HEALPix level form a "front" held structure-of-arrays
+// in a level buffer. A warp takes rays from the front in chunks (one ray per lane, lanes
+// refill from the chunk as their rays end), walks each ray from its start radius to its end
+// (Sec. 2.1: r_max(l), tau > tau_max or the grid boundary) and appends the four children of
+// every split ray to the next level's buffer with one warp-aggregated reservation.
+//
+// Two schedules share that routine:
+//   * plain: one launch per (source, level), fronts kept whole;
+//   * persistent: one cooperative launch for all sources. The launch loops over phases;
+//     each phase consumes the top part of the deepest non-empty level buffer, at most a
+//     quarter of the next buffer's capacity, so the children always fit. Deepest-first order
+//     keeps every buffer bounded, which is the memory role the paper's last-in-first-out ray
+//     stack plays (Sec. 2.2). A grid barrier with a bounded wait separates phases; the
+//     retired-ray weights 4^(l_max - l) are summed as the paper's destroy counter (Sec. 2.2).
+#pragma once
+
+#include "art_device.cuh"
+
+namespace art {
+
+// ---------------------------------------------------------------------------------------
+// HEALPix nested directions in FP64 (Gorski et al. 2005), rotated, split into hi + lo
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t even_bits(uint64_t x)
+{
+    x &= 0x5555555555555555ull;
+    x = (x | (x >> 1)) & 0x3333333333333333ull;
+    x = (x | (x >> 2)) & 0x0f0f0f0f0f0f0f0full;
+    x = (x | (x >> 4)) & 0x00ff00ff00ff00ffull;
+    x = (x | (x >> 8)) & 0x0000ffff0000ffffull;
+    x = (x | (x >> 16)) & 0x00000000ffffffffull;
+    return (uint32_t)x;
+}
+
+// cos and sin of pi * num / den (den > 0), exact at multiples of 1/2, cos = sin at 1/4.
+__device__ __forceinline__ void cossin_pi_frac(long long num, long long den, double& c, double& s)
+{
+    long long m = num % (2 * den);
+    if (m < 0) m += 2 * den;
+    double sgn_c = 1.0, sgn_s = 1.0;
+    if (m >= den) { m -= den; sgn_c = -1.0; sgn_s = -1.0; }  // shift by pi
+    if (2 * m > den) { m = den - m; sgn_c = -sgn_c; }        // reflect about pi/2
+    double cv, sv;
+    if (m == 0) { cv = 1.0; sv = 0.0; }
+    else if (2 * m == den) { cv = 0.0; sv = 1.0; }
+    else if (4 * m == den) { cv = 0.70710678118654752440; sv = cv; }
+    else sincospi((double)m / (double)den, &sv, &cv);
+    c = sgn_c * cv;
+    s = sgn_s * sv;
+}
+
+__global__ void k_directions(int level, unsigned long long npix, double r0, double r1, double r2,
+                             double r3, double r4, double r5, double r6, double r7, double r8,
+                             int rotate, float4* __restrict__ hi, float4* __restrict__ lo)
+{
+    unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    const long long ns = 1ll << level;
+    const unsigned long long nface = (unsigned long long)(ns * ns);
+    const int face = (int)(p / nface);
+    const unsigned long long q = p - (unsigned long long)face * nface;
+    const long long x = even_bits(q), y = even_bits(q >> 1);
+    const int row = face >> 2;                      // 0 north, 1 equator, 2 south
+    const long long ring = (long long)(row + 2) * ns - x - y - 1;
+    long long nr;
+    int shift = 0;
+    double z, st;
+    if (ring < ns || ring > 3 * ns) {
+        nr = ring < ns ? ring : 4 * ns - ring;
+        double a = (double)(nr * nr) / (3.0 * (double)(ns * ns));
+        z = ring < ns ? 1.0 - a : a - 1.0;
+        st = sqrt(a * (2.0 - a));
+    } else {
+        nr = ns;
+        shift = (int)((ring - ns) & 1);
+        z = (double)(4 * ns - 2 * ring) / (3.0 * (double)ns);
+        st = sqrt((1.0 - z) * (1.0 + z));
+    }
+    const int col = (row == 1) ? 2 * (face & 3) : 2 * (face & 3) + 1;
+    long long jp = (col * nr + x - y + 1 + shift) / 2;
+    if (jp > 4 * nr) jp -= 4 * nr;
+    if (jp < 1) jp += 4 * nr;
+    double c, s;
+    cossin_pi_frac(2 * jp - shift - 1, 4 * nr, c, s);
+    double v[3] = {st * c, st * s, z};
+    double w[3];
+    if (rotate) {
+        w[0] = r0 * v[0] + r1 * v[1] + r2 * v[2];
+        w[1] = r3 * v[0] + r4 * v[1] + r5 * v[2];
+        w[2] = r6 * v[0] + r7 * v[1] + r8 * v[2];
+    } else {
+        w[0] = v[0]; w[1] = v[1]; w[2] = v[2];
+    }
+    float h[3], l[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (fabs(w[a]) < 5.9604644775390625e-08) w[a] = 0.0;  // 2^-24
+        h[a] = __double2float_rn(w[a]);
+        l[a] = __double2float_rn(w[a] - (double)h[a]);
+    }
+    hi[p] = make_float4(h[0], h[1], h[2], 0.f);
+    lo[p] = make_float4(l[0], l[1], l[2], 0.f);
+}
+
+// chi per cell length (dx) in FP32 from the density fields; flags bad densities.
+__global__ void k_opacity(long long ncell, const float* __restrict__ nH0,
+                          const float* __restrict__ nH, double sH_dx, double sd_dx,
+                          float* __restrict__ chi, float* __restrict__ chiH,
+                          DevStats* __restrict__ st)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long step = (long long)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (; i < ncell; i += step) {
+        float a = nH0[i];
+        float b = nH ? nH[i] : 0.f;
+        bad = bad || !(a >= 0.f) || !(b >= 0.f) || isinf(a) || isinf(b);
+        double h = (double)a * sH_dx;
+        chi[i] = __double2float_rn(h + (double)b * sd_dx);
+        if (chiH) chiH[i] = __double2float_rn(h);
+    }
+    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicCAS(&st->error, 0, -1);
+}
+
+// Level-l0 rays of sources [s0, s0 + ns): pixel-major within each source.
+__global__ void k_inject(int s0, int nsrc, unsigned npix0, RayBuf B, unsigned long long* count)
+{
+    unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    unsigned long long n = (unsigned long long)nsrc * npix0;
+    if (i == 0) *count = n;
+    if (i >= n) return;
+    unsigned s = (unsigned)(i / npix0);
+    unsigned p = (unsigned)(i - (unsigned long long)s * npix0);
+    B.src[i] = s0 + s;
+    B.pix[i] = p;
+    B.L[i] = 0.f;     // filled from the source table when the ray starts
+    B.tau[i] = 0.f;
+}
+
+__device__ __forceinline__ void tally_flush(const Tally& T, DevStats* st)
+{
+    __shared__ double s_d[3];
+    __shared__ unsigned long long s_u[2];
+    if (threadIdx.x == 0) { s_d[0] = s_d[1] = s_d[2] = 0.0; s_u[0] = s_u[1] = 0ull; }
+    __syncthreads();
+    double e = T.escaped, d = T.dropped, a = T.absorbed;
+    unsigned long long c = T.crossings, w = T.destroy;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        e += __shfl_down_sync(kFull, e, off);
+        d += __shfl_down_sync(kFull, d, off);
+        a += __shfl_down_sync(kFull, a, off);
+        c += __shfl_down_sync(kFull, c, off);
+        w += __shfl_down_sync(kFull, w, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&s_d[0], e); atomicAdd(&s_d[1], d); atomicAdd(&s_d[2], a);
+        atomicAdd(&s_u[0], c); atomicAdd(&s_u[1], w);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&st->escaped, s_d[0]);
+        atomicAdd(&st->dropped, s_d[1]);
+        atomicAdd(&st->absorbed, s_d[2]);
+        atomicAdd(&st->crossings, s_u[0]);
+        atomicAdd(&st->destroy, s_u[1]);
+    }
+}
+
+// Starts the walk of ray i of level l. Returns true if the ray is inside the grid.
+__device__ __forceinline__ bool ray_begin(const TraceArgs& A, const LevelInfo& LV, const RayBuf& B,
+                                          int l, unsigned long long i, Walk& W, unsigned& s,
+                                          unsigned& p, float& L0, bool& splits)
+{
+    s = __ldcg(B.src + i);
+    p = __ldcg(B.pix + i);
+    const float4 sh = __ldg(&A.src[s].hi);
+    const float4 sl = __ldg(&A.src[s].lo);
+    L0 = (l == A.level0) ? sh.w : __ldcg(B.L + i);
+    const float tau0 = (l == A.level0) ? 0.f : __ldcg(B.tau + i);
+    const int lmax_s = __float_as_int(sl.w);
+    splits = l < lmax_s;
+    const float4 dh = __ldg(LV.dir_hi + p);
+    const float4 dl = __ldg(LV.dir_lo + p);
+    const df u[3] = {{sh.x, sl.x}, {sh.y, sl.y}, {sh.z, sl.z}};
+    const df n[3] = {{dh.x, dl.x}, {dh.y, dl.y}, {dh.z, dl.z}};
+    const df te = splits ? LV.rmax : df{kBig, 0.f};
+    bool inside = walk_start(W, A, u, n, LV.r0, te);
+    W.L = L0;
+    W.tau = tau0;
+    W.chi = inside ? __ldg(A.chi + W.idx) : 0.f;
+    return inside;
+}
+
+// Processes rays [cursor .. end) of level l (cursor advanced atomically by warps, `chunk`
+// rays at a time). Warp-uniform: every lane of the warp must call it.
+__device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
+                         unsigned long long end, Tally& T)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lt = (1u << lane) - 1u;
+    const LevelInfo LV = A.levels[l];
+    const RayBuf B = A.buf[l];
+    const RayBuf C = A.buf[l + 1];
+    unsigned long long* child_count = &A.sched->count[l + 1];
+
+    unsigned long long wnext = 0, wend = 0;
+    bool more = true;
+    bool active = false;
+    Walk W;
+    unsigned s = 0, p = 0;
+    float L0 = 0.f;
+    bool splits = false;
+    unsigned ncross = 0;
+
+    for (;;) {
+        // refill idle lanes from the warp's chunk, fetching chunks as needed
+        unsigned need = __ballot_sync(kFull, !active);
+        while (need && more) {
+            if (wnext >= wend) {
+                unsigned long long b = 0;
+                if (lane == 0) b = atomicAdd(cursor, (unsigned long long)A.chunk);
+                b = __shfl_sync(kFull, b, 0);
+                if (b >= end) { more = false; break; }
+                wnext = b;
+                wend = min(b + (unsigned long long)A.chunk, end);
+            }
+            const unsigned avail = (unsigned)min(wend - wnext, 32ull);
+            const unsigned rank = __popc(need & lt);
+            if (!active && rank < avail) {
+                bool inside = ray_begin(A, LV, B, l, wnext + rank, W, s, p, L0, splits);
+                if (inside) {
+                    active = true;
+                } else {  // starts outside the grid: escapes with its full luminosity
+                    T.escaped += (double)L0;
+                    T.destroy += LV.destroy_w;
+                }
+            }
+            wnext += min(avail, (unsigned)__popc(need));
+            need = __ballot_sync(kFull, !active);
+        }
+        if (!__any_sync(kFull, active)) break;
+
+        bool want_split = false;
+#pragma unroll 1
+        for (int k = 0; k < 4; ++k) {
+            int cell = -1;
+            float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (active) {
+                StepOut o = walk_step<false>(W, A.chi, A.tau_max);
+                if (o.cell >= 0) {
+                    cell = o.cell;
+                    dv = make_float4(o.G, o.dL * W.n[0], o.dL * W.n[1], o.dL * W.n[2]);
+                    ++ncross;
+                }
+                if (o.ev != EV_NONE) {
+                    active = false;
+                    T.absorbed += (double)L0 - (double)W.L;
+                    if (o.ev == EV_SPLIT) {
+                        want_split = true;
+                    } else {
+                        if (o.ev == EV_EXIT) T.escaped += (double)W.L;
+                        else T.dropped += (double)W.L;
+                        T.destroy += LV.destroy_w;
+                    }
+                }
+            }
+            deposit_warp(A.acc, cell, dv);
+        }
+        // append the children of split rays to the next level
+        const unsigned sm = __ballot_sync(kFull, want_split);
+        if (sm) {
+            unsigned long long base = 0;
+            const int leader = __ffs(sm) - 1;
+            if ((int)lane == leader) base = atomicAdd(child_count, 4ull * __popc(sm));
+            base = __shfl_sync(kFull, base, leader);
+            if (want_split) {
+                unsigned long long slot = base + 4ull * __popc(sm & lt);
+                if (slot + 4 <= C.cap) {
+                    const float Lc = 0.25f * W.L;
+                    *reinterpret_cast<uint4*>(C.src + slot) = make_uint4(s, s, s, s);
+                    *reinterpret_cast<uint4*>(C.pix + slot) =
+                        make_uint4(4 * p, 4 * p + 1, 4 * p + 2, 4 * p + 3);
+                    *reinterpret_cast<float4*>(C.L + slot) = make_float4(Lc, Lc, Lc, Lc);
+                    *reinterpret_cast<float4*>(C.tau + slot) =
+                        make_float4(W.tau, W.tau, W.tau, W.tau);
+                } else {
+                    atomicCAS(&A.stats->error, 0, -3);  // ART_EQUEUE_OVERFLOW
+                }
+            }
+        }
+    }
+    T.crossings += ncross;
+}
+
+// Plain schedule: all rays of level l currently in its buffer.
+__global__ void k_trace_level(const __grid_constant__ TraceArgs A, int l)
+{
+    Tally T = {0.0, 0.0, 0.0, 0ull, 0ull};
+    // a front that overflowed (status set by the writer) is cut at the buffer capacity
+    const unsigned long long end =
+        min(*((volatile unsigned long long*)&A.sched->count[l]), A.buf[l].cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && end > 0) {
+        atomicAdd(&A.stats->rays_per_level[l], end);
+        atomicAdd(&A.stats->rays_total, end);
+        atomicMax(&A.stats->level_reached, l);
+    }
+    run_rays(A, l, &A.sched->cursor[l], end, T);
+    tally_flush(T, A.stats);
+}
+
+// Resets the per-level counters of the plain schedule before the next source.
+__global__ void k_reset_counts(Sched* sc)
+{
+    int t = threadIdx.x;
+    if (t < kNL) { sc->count[t] = 0; sc->cursor[t] = 0; }
+}
+
+// Grid-wide barrier for a cooperative launch. Every wait is bounded by wait_ns of
+// %globaltimer; on expiry the block records ART_ETIMEOUT and the barrier returns false.
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ bool grid_barrier(Sched* sc, DevStats* st, long long wait_ns)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned* gen = &sc->bar_gen;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&sc->bar_count, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            atomicExch(&sc->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&sc->bar_gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*gen == g) {
+                if (wait_ns < 0 || (long long)(global_ns() - t0) > wait_ns) {
+                    atomicCAS(&st->error, 0, -4);  // ART_ETIMEOUT
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(200);
+            }
+        }
+        __threadfence();
+        if (*((volatile int*)&st->error) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Persistent schedule: all sources, all levels, one cooperative launch.
+__global__ void k_trace_persistent(const __grid_constant__ TraceArgs A)
+{
+    Tally T = {0.0, 0.0, 0.0, 0ull, 0ull};
+    Sched* sc = A.sched;
+    __shared__ int s_level;
+    __shared__ unsigned long long s_end;
+    for (;;) {
+        if (!grid_barrier(sc, A.stats, A.wait_ns)) break;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            volatile unsigned long long* cnt = sc->count;
+            int l = -1;
+            for (int k = A.lmax_glob; k >= A.level0; --k)
+                if (cnt[k] > 0) { l = k; break; }
+            if (l < 0) {
+                sc->done = 1;
+            } else {
+                unsigned long long have = min(cnt[l], A.buf[l].cap);
+                unsigned long long take = have;
+                if (l < A.lmax_glob) take = min(have, A.buf[l + 1].cap / 4);
+                sc->phase_level = l;
+                sc->phase_begin = have - take;
+                sc->phase_end = have;
+                sc->cursor[l] = have - take;
+                cnt[l] = have - take;
+                A.stats->rays_per_level[l] += take;
+                A.stats->rays_total += take;
+                if (l > A.stats->level_reached) A.stats->level_reached = l;
+            }
+            __threadfence();
+        }
+        if (!grid_barrier(sc, A.stats, A.wait_ns)) break;
+        if (threadIdx.x == 0) {
+            volatile Sched* v = sc;
+            s_level = v->done ? -1 : v->phase_level;
+            s_end = v->phase_end;
+        }
+        __syncthreads();
+        const int l = s_level;
+        if (l < 0) break;
+        run_rays(A, l, &sc->cursor[l], s_end, T);
+    }
+    tally_flush(T, A.stats);
+}
+
+// Gamma, force and energy from the accumulator (SoA outputs).
+__global__ void k_finalize(long long ncell, const float4* __restrict__ acc, float gscale,
+                           float fscale, float escale, float* __restrict__ gamma,
+                           float* __restrict__ force, float* __restrict__ energy)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long step = (long long)gridDim.x * blockDim.x;
+    for (; i < ncell; i += step) {
+        float4 a = __ldcs(acc + i);
+        gamma[i] = gscale * a.x;
+        if (force) {
+            force[i] = fscale * a.y;
+            force[ncell + i] = fscale * a.z;
+            force[2 * ncell + i] = fscale * a.w;
+        }
+        if (energy) energy[i] = escale * a.x;
+    }
+}
+
+}  // namespace art

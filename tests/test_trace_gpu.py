@@ -1,0 +1,179 @@
+"""GPU forward trace vs the FP64 oracle (per-cell gamma and force, tallies, conservation),
+both schedules, on the synthetic workloads and edge cases."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_1711_06277_gb300 import synth
+from tests import parity as PA
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def art():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1711_06277_gb300 import art as A
+    return A
+
+
+def _run(A, nH0, pos, L, dx, params, nH=None, lo=(0.0, 0.0, 0.0)):
+    dev = torch.device("cuda")
+    t0 = torch.as_tensor(np.ascontiguousarray(nH0, dtype=np.float32), device=dev)
+    t1 = None if nH is None else torch.as_tensor(np.ascontiguousarray(nH, dtype=np.float32), device=dev)
+    g = A.Grid(t0, dx, lo=lo, nH=t1)
+    g.add_sources(pos, L)
+    out = g.trace(params, force=True, energy=True)
+    res = {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in out.items()}
+    g.close()
+    return res
+
+
+def _oracle(nH0, pos, L, dx, p, nH=None, threads=8):
+    prob = O.Problem(nH0=nH0, pos=pos, L=L, dx=dx, nH=nH, sigma_H=p.sigma_H,
+                     sigma_d=p.sigma_d, level0=p.level0, level_cap=p.level_max, m_ray=p.m_ray,
+                     tau_max=p.tau_max, rot=p.rot)
+    return O.trace(prob, nthreads=threads)
+
+
+def _check(res, ref, nH0, p, nH=None, exact_counts=True):
+    st = res["stats"]
+    assert st["status"] == 0
+    PA.compare_field(res["gamma"], ref.gamma, what="gamma")
+    PA.compare_field(res["energy"], ref.energy, what="energy")
+    PA.compare_force(res["force"], ref.force)
+    if exact_counts:
+        assert st["crossings"] == ref.crossings
+        assert st["rays_per_level"] == ref.rays_per_level.tolist()
+    else:
+        assert abs(st["crossings"] - ref.crossings) <= 1e-5 * ref.crossings
+    assert st["destroy"] == st["destroy_expected"] == ref.destroy_expected
+    assert st["level_max"] == ref.level_max
+    L_in = ref.L_in
+    assert abs(st["L_escaped"] - ref.escaped) <= PA.CONS * L_in
+    assert abs(st["L_dropped"] - ref.dropped) <= PA.CONS * L_in
+    assert abs(st["L_absorbed"] - ref.absorbed) <= PA.CONS * L_in
+    chi = nH0.astype(np.float32).astype(np.float64) * p.sigma_H
+    if nH is not None:
+        chi = chi + nH.astype(np.float32).astype(np.float64) * p.sigma_d
+    G_phys = res["energy"] * ref.dV
+    assert PA.conservation(chi, G_phys, st) <= PA.CONS
+
+
+@pytest.mark.parametrize("schedule", ["persistent", "plain"])
+def test_config1_uniform_32(art, schedule):
+    n = 32
+    nH0 = np.ones((n, n, n))
+    p = art.Params(level0=4, m_ray=4.0, tau_max=30.0, sigma_H=5.0, schedule=schedule)
+    pos, L = np.array([[0.5, 0.5, 0.5]]), np.array([1.0])
+    res = _run(art, nH0, pos, L, 1.0 / n, p)
+    ref = _oracle(nH0, pos, L, 1.0 / n, p)
+    assert ref.near_tie_rays == 0
+    _check(res, ref, nH0, p)
+
+
+@pytest.mark.parametrize("schedule", ["persistent", "plain"])
+def test_config2_lognormal_128(art, schedule):
+    n = 128
+    rho = synth.lognormal_field(n, 1.5, seed=1)
+    p = art.Params(level0=4, m_ray=4.0, tau_max=30.0, sigma_H=10.0, schedule=schedule)
+    pos = synth.cell_centre_position(n, seed=1)
+    L = np.array([1.0])
+    res = _run(art, rho, pos, L, 1.0 / n, p)
+    ref = _oracle(rho, pos, L, 1.0 / n, p)
+    _check(res, ref, rho, p, exact_counts=ref.near_tie_rays == 0)
+
+
+def test_config2_vacuum_128(art):
+    n = 128
+    p = art.Params(level0=4, m_ray=4.0, tau_max=30.0, sigma_H=10.0)
+    pos = synth.cell_centre_position(n, seed=1)
+    res = _run(art, np.zeros((n, n, n)), pos, np.array([1.0]), 1.0 / n, p)
+    ref = _oracle(np.zeros((n, n, n)), pos, np.array([1.0]), 1.0 / n, p)
+    PA.compare_field(res["energy"], ref.energy, what="vacuum energy")
+    assert res["stats"]["crossings"] == ref.crossings
+    # inverse-square law, paper's accuracy band (Sec. 3.2)
+    c = np.arange(n) + 0.5
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    u = pos[0] * n
+    rr = np.sqrt((x - u[0]) ** 2 + (y - u[1]) ** 2 + (z - u[2]) ** 2)
+    sel = (rr > 4) & (rr < 40)
+    err = np.abs(res["energy"][sel] * 4 * np.pi * (rr[sel] / n) ** 2 - 1)
+    assert 0.005 < np.median(err) < 0.04
+
+
+@pytest.mark.parametrize("schedule", ["persistent", "plain"])
+def test_multisource_dust_rotation_64(art, schedule):
+    n = 64
+    rho = synth.lognormal_field(n, 1.5, seed=7)
+    pos = synth.uniform_positions(8, seed=7)
+    L = synth.power_law_luminosities(8, seed=7)
+    R = synth.random_rotation(7)
+    p = art.Params(level0=3, m_ray=4.0, tau_max=30.0, sigma_H=6.0, sigma_d=2.0, rot=R,
+                   schedule=schedule)
+    nH = 1.7 * rho
+    res = _run(art, 0.5 * rho, pos, L, 1.0 / n, p, nH=nH)
+    ref = _oracle(0.5 * rho, pos, L, 1.0 / n, p, nH=nH)
+    _check(res, ref, 0.5 * rho, p, nH=nH, exact_counts=ref.near_tie_rays == 0)
+
+
+def test_small_queue_persistent_matches(art):
+    # a front capacity far below the ray count forces many depth-first phases
+    n = 48
+    rho = synth.lognormal_field(n, 1.0, seed=3)
+    pos = synth.uniform_positions(3, seed=3)
+    L = synth.power_law_luminosities(3, seed=3)
+    p = art.Params(level0=2, tau_max=30.0, sigma_H=4.0, queue_capacity=1000, chunk=32)
+    res = _run(art, rho, pos, L, 1.0 / n, p)
+    ref = _oracle(rho, pos, L, 1.0 / n, p)
+    _check(res, ref, rho, p, exact_counts=ref.near_tie_rays == 0)
+
+
+@pytest.mark.parametrize("shape,level0,lmax", [((1, 1, 1), 0, -1), ((5, 9, 3), 1, -1),
+                                               ((17, 16, 33), 8, -1), ((20, 20, 20), 2, 2)])
+def test_odd_shapes_and_levels(art, shape, level0, lmax):
+    nz, ny, nx = shape
+    rng = np.random.default_rng(sum(shape) + level0)
+    rho = rng.random(shape) * 3
+    dx = 0.1
+    lo = (-0.3, 0.2, 1.0)
+    box = np.array([nx, ny, nz]) * dx
+    pos = np.asarray(lo) + box * rng.uniform(0.05, 0.95, size=(2, 3))
+    L = np.array([0.3, 2.0])
+    p = art.Params(level0=level0, level_max=lmax, tau_max=30.0, sigma_H=1.5)
+    res = _run(art, rho, pos, L, dx, p, lo=lo)
+    prob = O.Problem(nH0=rho, pos=pos, L=L, dx=dx, lo=lo, sigma_H=1.5, level0=level0,
+                     level_cap=lmax, tau_max=30.0)
+    ref = O.trace(prob, nthreads=8)
+    _check(res, ref, rho, p, exact_counts=ref.near_tie_rays == 0)
+
+
+def test_source_near_faces_and_small_tau_max(art):
+    n = 24
+    rho = np.ones((n, n, n))
+    eps = 1e-7
+    pos = np.array([[eps, 0.5, 0.5], [1 - eps, 1 - eps, eps], [0.3, 0.6, 0.9]])
+    L = np.array([1.0, 1.0, 2.0])
+    p = art.Params(level0=2, tau_max=0.3, sigma_H=8.0)
+    res = _run(art, rho, pos, L, 1.0 / n, p)
+    ref = _oracle(rho, pos, L, 1.0 / n, p)
+    assert ref.dropped > 0
+    _check(res, ref, rho, p, exact_counts=ref.near_tie_rays == 0)
+
+
+def test_integer_tallies_deterministic(art):
+    n = 64
+    rho = synth.lognormal_field(n, 2.0, seed=9)
+    pos = synth.uniform_positions(16, seed=9)
+    L = synth.power_law_luminosities(16, seed=9)
+    p = art.Params(level0=4, tau_max=30.0, sigma_H=10.0)
+    a = _run(art, rho, pos, L, 1.0 / n, p)
+    b = _run(art, rho, pos, L, 1.0 / n, p)
+    for k in ("crossings", "rays_total", "rays_per_level", "destroy"):
+        assert a["stats"][k] == b["stats"][k]
+    np.testing.assert_allclose(a["gamma"], b["gamma"], rtol=1e-5, atol=1e-6 * a["gamma"].max())
