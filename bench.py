@@ -37,6 +37,9 @@ CONFIGS = {
                            alpha=2e-4, x0=1e-3),
     "c3_256_64src": dict(n=256, sigma_ln=2.0, nsrc=64, seed=3, nbar=1.0, sigma_H=10.0,
                          alpha=None, x0=1.0),
+    # small case of the same kernel for ncu captures (a few hundred MB on the device)
+    "c3_256_8src": dict(n=256, sigma_ln=2.0, nsrc=8, seed=3, nbar=1.0, sigma_H=10.0,
+                        alpha=None, x0=1.0),
 }
 
 

@@ -1,7 +1,399 @@
-// art_adjoint.cu -- placeholder replaced by the reverse-sweep kernels.
+// art_adjoint.cu -- hand-written adjoint of the forward trace for loss = sum_c w_c gamma_c
+// (new; the paper has no adjoint). Gradients with respect to log n_H0 per cell and to every
+// source luminosity.
+//
+// For a segment j of a ray in cell c, with G_j = L_in ds phi(dtau), dtau = chi ds and
+// dtauH = n_H0 sigma_H ds (the part of dtau that scales with n_H0):
+//   d loss / d log n_H0[c] += dtauH (w_c k L_in ds phi'(dtau) - S_after(j)),
+// where k converts G to gamma and S_after(j) is the weighted sum w k G over every later
+// segment of the ray and over all of its descendants (their entering luminosity carries the
+// factor e^-dtau of segment j). Split points and tau_max retirement are held fixed.
+//
+// Nothing is stored per segment. Rays are traced with unit source luminosity (the loss is
+// linear in each L_s; gradients are scaled by L_s when deposited) in a reverse-level sweep of
+// the persistent schedule:
+//   expand phase (level l chunk): pass 1 replays each ray and sums its own weighted G; a
+//     split ray stores that sum and emits its children (with a back-pointer); a ray that
+//     ends there replays again at once (pass 2) and deposits its gradients;
+//   collapse phase (the same chunk, once every descendant is finished): each split ray
+//     replays (pass 2) with S = own + children's sums, depositing its gradients, and adds its
+//     total to its parent.
+// The phase order is deepest-first, as in the forward schedule, so children always finish
+// before their parents' collapse and every level buffer stays bounded.
+#include <cmath>
+#include <cstring>
+
 #include "art.h"
-extern "C" int art_trace_backward(art_grid*, const art_params*, const float*, float*, double*,
-                                  art_stats*)
+#include "art_internal.h"
+
+using namespace art;
+
+namespace {
+
+enum : int { PH_EXPAND = 0, PH_COLLAPSE = 1 };
+
+// d/dx of (1 - e^-x)/x. Taylor series below 1 (no cancellation), closed form above.
+__device__ __forceinline__ float dphi_of(float x, float em)
 {
-    return ART_ESTATE;
+    if (x < 1.f) {
+        float r = 1.f / 518918400.f;
+        r = fmaf(r, x, -1.f / 43545600.f);
+        r = fmaf(r, x, 1.f / 3991680.f);
+        r = fmaf(r, x, -1.f / 403200.f);
+        r = fmaf(r, x, 1.f / 45360.f);
+        r = fmaf(r, x, -1.f / 5760.f);
+        r = fmaf(r, x, 1.f / 840.f);
+        r = fmaf(r, x, -1.f / 144.f);
+        r = fmaf(r, x, 1.f / 30.f);
+        r = fmaf(r, x, -1.f / 8.f);
+        r = fmaf(r, x, 1.f / 3.f);
+        return fmaf(r, x, -0.5f);
+    }
+    return ((1.f + x) * (1.f + em) - 1.f) / (x * x);
+}
+
+// Scalar version of the warp-merged deposit: runs of equal cells in lane order are summed
+// and written by their first lane.
+__device__ __forceinline__ void deposit_warp1(float* __restrict__ out, int cell, float v)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    int prev = __shfl_up_sync(kFull, cell, 1);
+    bool dup = lane > 0 && cell >= 0 && prev == cell;
+    unsigned dups = __ballot_sync(kFull, dup);
+    if (dups) {
+        unsigned heads = ~dups;
+        unsigned after = lane == 31 ? 0u : heads & ~((2u << lane) - 1u);
+        int run_end = after ? __ffs(after) - 1 : 32;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            float o = __shfl_down_sync(kFull, v, off);
+            if ((int)lane + off < run_end) v += o;
+        }
+        if (dup) cell = -1;
+    }
+    if (cell >= 0) atomicAdd(out + cell, v);
+}
+
+struct DLacc {
+    double v;
+    unsigned src;
+};
+
+__device__ __forceinline__ void dl_add(DLacc& D, double* dL, unsigned s, double own)
+{
+    if (s != D.src) {
+        if (D.src != 0xffffffffu && D.v != 0.0) atomicAdd(dL + D.src, D.v);
+        D.src = s;
+        D.v = 0.0;
+    }
+    D.v += own;
+}
+
+__device__ __forceinline__ df df_of(double v)
+{
+    const float h = __double2float_rn(v);
+    return {h, __double2float_rn(v - (double)h)};
+}
+
+// One phase of the reverse sweep on rays [cursor .. end) of level l. Warp-uniform.
+__device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long long* cursor,
+                            unsigned long long end, Tally& T, DLacc& D)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lt = (1u << lane) - 1u;
+    const LevelInfo LV = A.levels[l];
+    const RayBuf B = A.buf[l];
+    const RayBuf C = A.buf[l + 1];
+    const RayBuf P = l > A.level0 ? A.buf[l - 1] : A.buf[l];
+    unsigned long long* child_count = &A.sched->count[l + 1];
+    const float gs = A.gscale;
+    const int sy = A.nx, sz = A.nx * A.ny;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+
+    unsigned long long wnext = 0, wend = 0;
+    bool more = true;
+    int mode = 0;  // 0 idle, 1 pass 1, 2 pass 2
+    Walk W;
+    unsigned s = 0, p = 0;
+    unsigned long long slot = 0;
+    float L0 = 0.f, Ls = 0.f;
+    df own = {0.f, 0.f};   // own weighted sum (pass 1), kept for dL in pass 2
+    double total = 0.0;    // own + descendants (pass 2)
+    df rem = {0.f, 0.f};   // weighted sum over what follows the current segment (pass 2)
+    bool splits = false;
+    unsigned ncross = 0;
+
+    for (;;) {
+        unsigned need = __ballot_sync(kFull, mode == 0);
+        while (need && more) {
+            if (wnext >= wend) {
+                unsigned long long b = 0;
+                if (lane == 0) b = atomicAdd(cursor, (unsigned long long)A.chunk);
+                b = __shfl_sync(kFull, b, 0);
+                if (b >= end) { more = false; break; }
+                wnext = b;
+                wend = min(b + (unsigned long long)A.chunk, end);
+            }
+            const unsigned avail = (unsigned)min(wend - wnext, 32ull);
+            const unsigned rank = __popc(need & lt);
+            if (mode == 0 && rank < avail) {
+                slot = wnext + rank;
+                if (kind == PH_EXPAND) {
+                    const bool inside = ray_begin(A, LV, B, l, slot, W, s, p, L0, splits);
+                    Ls = __ldg(A.srcL + s);
+                    if (inside) {
+                        mode = 1;
+                        own = {0.f, 0.f};
+                    } else {  // no segment at all: a finished leaf with zero sums
+                        T.escaped += (double)L0;
+                        T.destroy += LV.destroy_w;
+                        B.own[slot] = nan;
+                    }
+                } else {
+                    const double ov = __ldcg(B.own + slot);
+                    if (ov == ov) {  // a split ray waiting for its collapse
+                        total = ov + __ldcg(B.sub + slot);
+                        own = df_of(ov);
+                        rem = df_of(total);
+                        ray_begin(A, LV, B, l, slot, W, s, p, L0, splits);
+                        Ls = __ldg(A.srcL + s);
+                        mode = 2;
+                    }
+                }
+            }
+            wnext += min(avail, (unsigned)__popc(need));
+            need = __ballot_sync(kFull, mode == 0);
+        }
+        if (!__any_sync(kFull, mode != 0)) break;
+
+        bool want_split = false;
+#pragma unroll 1
+        for (int k = 0; k < 4; ++k) {
+            int cell = -1;
+            float val = 0.f;
+            if (mode != 0) {
+                const float wv = __ldg(A.w + W.idx);
+                const float hv = mode == 2 ? __ldg(A.chiH + W.idx) : 0.f;
+                const StepOut o = walk_step<false>(W, splits, LV.rmax, sy, sz, A.chi, A.tau_max);
+                if (o.cell >= 0) {
+                    const float g = wv * gs * o.G;
+                    if (mode == 1) {
+                        own = df_add(own, {g, 0.f});
+                        ++ncross;
+                    } else {
+                        rem = df_add(rem, {-g, 0.f});
+                        const float after = rem.hi + rem.lo;
+                        const float dphi = dphi_of(o.dtau, -o.dtau * o.phi);
+                        val = Ls * hv * o.ds * (wv * gs * o.Lin * o.ds * dphi - after);
+                        cell = o.cell;
+                    }
+                }
+                if (o.ev != EV_NONE) {
+                    if (mode == 1) {
+                        if (o.ev == EV_SPLIT) {
+                            want_split = true;
+                            B.own[slot] = (double)own.hi + (double)own.lo;
+                            B.sub[slot] = 0.0;
+                            mode = 0;
+                        } else {
+                            if (o.ev == EV_EXIT) T.escaped += (double)W.L;
+                            else T.dropped += (double)W.L;
+                            T.destroy += LV.destroy_w;
+                            B.own[slot] = nan;  // finished within this phase
+                            total = (double)own.hi + (double)own.lo;
+                            rem = own;
+                            ray_begin(A, LV, B, l, slot, W, s, p, L0, splits);
+                            mode = 2;
+                        }
+                    } else {
+                        if (l > A.level0) atomicAdd(P.sub + __ldcg(B.parent + slot), total);
+                        dl_add(D, A.dL, s, (double)own.hi + (double)own.lo);
+                        mode = 0;
+                    }
+                }
+            }
+            deposit_warp1(A.grad, cell, val);
+        }
+        const unsigned sm = __ballot_sync(kFull, want_split);
+        if (sm) {
+            unsigned long long base = 0;
+            const int leader = __ffs(sm) - 1;
+            if ((int)lane == leader) base = atomicAdd(child_count, 4ull * __popc(sm));
+            base = __shfl_sync(kFull, base, leader);
+            if (want_split) {
+                unsigned long long cs = base + 4ull * __popc(sm & lt);
+                if (cs + 4 <= C.cap) {
+                    const float Lc = 0.25f * W.L;
+                    const unsigned ps = (unsigned)slot;
+                    *reinterpret_cast<uint4*>(C.src + cs) = make_uint4(s, s, s, s);
+                    *reinterpret_cast<uint4*>(C.pix + cs) =
+                        make_uint4(4 * p, 4 * p + 1, 4 * p + 2, 4 * p + 3);
+                    *reinterpret_cast<float4*>(C.L + cs) = make_float4(Lc, Lc, Lc, Lc);
+                    *reinterpret_cast<float4*>(C.tau + cs) = make_float4(W.tau, W.tau, W.tau, W.tau);
+                    *reinterpret_cast<uint4*>(C.parent + cs) = make_uint4(ps, ps, ps, ps);
+                } else {
+                    atomicCAS(&A.stats->error, 0, -3);
+                }
+            }
+        }
+    }
+    T.crossings += ncross;
+}
+
+__global__ void k_backward_persistent(const __grid_constant__ TraceArgs A)
+{
+    Tally T = {0.0, 0.0, 0ull, 0ull};
+    DLacc D = {0.0, 0xffffffffu};
+    Sched* sc = A.sched;
+    __shared__ int s_level, s_kind;
+    __shared__ unsigned long long s_end;
+    for (;;) {
+        if (!grid_barrier(sc, A.stats, A.wait_ns)) break;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            volatile Sched* v = sc;
+            int l = -1;
+            for (int k = A.lmax_glob; k >= A.level0; --k)
+                if (v->count[k] > 0 || v->chunk_state[k] == 1) { l = k; break; }
+            if (l < 0) {
+                v->done = 1;
+            } else if (v->chunk_state[l] == 1) {
+                v->chunk_state[l] = 0;
+                v->phase_level = l;
+                v->phase_kind = PH_COLLAPSE;
+                v->phase_end = v->chunk_end[l];
+                v->cursor[l] = v->chunk_begin[l];
+            } else {
+                unsigned long long have = min(v->count[l], A.buf[l].cap);
+                unsigned long long take = have;
+                if (l < A.lmax_glob) take = min(have, A.buf[l + 1].cap / 4);
+                const unsigned long long b = have - take;
+                v->count[l] = b;
+                v->phase_level = l;
+                v->phase_kind = PH_EXPAND;
+                v->phase_end = have;
+                v->cursor[l] = b;
+                if (l < A.lmax_glob) {
+                    v->chunk_state[l] = 1;
+                    v->chunk_begin[l] = b;
+                    v->chunk_end[l] = have;
+                }
+                A.stats->rays_per_level[l] += take;
+                A.stats->rays_total += take;
+                if (l > A.stats->level_reached) A.stats->level_reached = l;
+            }
+            __threadfence();
+        }
+        if (!grid_barrier(sc, A.stats, A.wait_ns)) break;
+        if (threadIdx.x == 0) {
+            volatile Sched* v = sc;
+            s_level = v->done ? -1 : v->phase_level;
+            s_kind = v->phase_kind;
+            s_end = v->phase_end;
+        }
+        __syncthreads();
+        const int l = s_level;
+        if (l < 0) break;
+        run_adjoint(A, l, s_kind, &sc->cursor[l], s_end, T, D);
+    }
+    if (D.src != 0xffffffffu && D.v != 0.0) atomicAdd(A.dL + D.src, D.v);
+    tally_flush(T, A.stats);
+}
+
+__global__ void k_inject_all(int nsrc, unsigned npix0, RayBuf B, unsigned long long* count)
+{
+    unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    unsigned long long n = (unsigned long long)nsrc * npix0;
+    if (i == 0) *count = n;
+    if (i >= n) return;
+    unsigned s = (unsigned)(i / npix0);
+    B.src[i] = s;
+    B.pix[i] = (unsigned)(i - (unsigned long long)s * npix0);
+    B.L[i] = 0.f;
+    B.tau[i] = 0.f;
+}
+
+int status_of(cudaError_t e)
+{
+    if (e == cudaSuccess) return ART_OK;
+    return e == cudaErrorMemoryAllocation ? ART_ENOMEM : ART_ECUDA;
+}
+
+}  // namespace
+
+extern "C" int art_trace_backward(art_grid* g, const art_params* p, const float* d_w,
+                                  float* d_dlog_nH0, double* d_dL, art_stats* h_stats)
+{
+    if (!g || !d_w || !d_dlog_nH0) return ART_EINVAL;
+    int rc = check_params(p);
+    if (rc) return rc;
+    // the reverse sweep always runs the persistent schedule (all base rays in one buffer)
+    art_params pp = *p;
+    pp.schedule = ART_SCHED_PERSISTENT;
+    p = &pp;
+    const int ns = (int)g->L.size();
+    if (ns == 0) return ART_ESTATE;
+    cudaStream_t st = g->stream;
+    if ((rc = status_of(cudaMemsetAsync(g->d_stats, 0, sizeof(DevStats), st)))) return rc;
+    if (!g->d_chiH && (rc = status_of(cudaMalloc((void**)&g->d_chiH, sizeof(float) * g->ncell))))
+        return rc;
+    rc = prepare_trace(g, p, true);
+    if (rc) return rc;
+    if ((size_t)ns > g->srcL_cap) {
+        if (g->d_srcL) cudaFree(g->d_srcL);
+        g->d_srcL = nullptr;
+        g->srcL_cap = 0;
+        if ((rc = status_of(cudaMalloc((void**)&g->d_srcL, sizeof(float) * ns)))) return rc;
+        if ((rc = status_of(cudaMalloc((void**)&g->d_dL_scratch, sizeof(double) * ns)))) return rc;
+        g->srcL_cap = ns;
+    }
+    g->h_srcL.resize(ns);
+    for (int s = 0; s < ns; ++s) g->h_srcL[s] = (float)g->L[s];
+    if ((rc = status_of(cudaMemcpyAsync(g->d_srcL, g->h_srcL.data(), sizeof(float) * ns,
+                                        cudaMemcpyHostToDevice, st))))
+        return rc;
+    double* dL = d_dL ? d_dL : g->d_dL_scratch;
+    if ((rc = status_of(cudaMemsetAsync(dL, 0, sizeof(double) * ns, st)))) return rc;
+    if ((rc = status_of(cudaMemsetAsync(d_dlog_nH0, 0, sizeof(float) * g->ncell, st)))) return rc;
+    if ((rc = status_of(cudaMemsetAsync(g->d_sched, 0, sizeof(Sched), st)))) return rc;
+    const int l0 = p->level0;
+    const unsigned npix0 = 12u << (2 * l0);
+    const unsigned long long nb = (unsigned long long)ns * npix0;
+    k_inject_all<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(ns, npix0, g->buf[l0],
+                                                            &g->d_sched->count[l0]);
+    if ((rc = status_of(cudaGetLastError()))) return rc;
+    TraceArgs A = make_args(g, p);
+    A.w = d_w;
+    A.grad = d_dlog_nH0;
+    A.dL = dL;
+    A.srcL = g->d_srcL;
+    const double dV = g->dx * g->dx * g->dx;
+    A.gscale = (float)(p->sigma_H * g->dx / dV);
+    const int threads = p->block_threads > 0 ? p->block_threads : 256;
+    int per_sm = 0;
+    if ((rc = status_of(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_persistent,
+                                                                      threads, 0))))
+        return rc;
+    if (per_sm < 1) return ART_EINVAL;
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(per_sm * g->sms);
+    cfg.blockDim = dim3(threads);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if ((rc = status_of(cudaLaunchKernelEx(&cfg, k_backward_persistent, A)))) return rc;
+    if ((rc = status_of(cudaMemcpyAsync(g->h_stats, g->d_stats, sizeof(DevStats),
+                                        cudaMemcpyDeviceToHost, st))))
+        return rc;
+    g->last_L_in = 0.0;
+    for (double v : g->L) g->last_L_in += v;
+    g->last_lmax = g->lmax_glob;
+    g->destroy_expected = (unsigned long long)ns * (12ull << (2 * g->lmax_glob));
+    g->last_kind = 1;
+    g->traced = true;
+    if (h_stats) return finish_stats(g, h_stats);
+    return ART_OK;
 }

@@ -147,9 +147,8 @@ int prepare_trace(art_grid* g, const art_params* p, bool adjoint)
     }
     for (int l = l0; l <= lmax_glob; ++l) {
         const unsigned long long npix = 12ull << (2 * l);
-        if (!g->dir_hi[l]) {
-            int rc = dev_alloc(&g->dir_hi[l], npix);
-            if (!rc) rc = dev_alloc(&g->dir_lo[l], npix);
+        if (!g->dir[l]) {
+            int rc = dev_alloc(&g->dir[l], 3 * npix);
             if (rc) return rc;
             g->dir_built[l] = false;
         }
@@ -158,7 +157,7 @@ int prepare_trace(art_grid* g, const art_params* p, bool adjoint)
             unsigned blocks = (unsigned)((npix + 255) / 256);
             k_directions<<<blocks, 256, 0, g->stream>>>(l, npix, r[0], r[1], r[2], r[3], r[4],
                                                         r[5], r[6], r[7], r[8], rotate ? 1 : 0,
-                                                        g->dir_hi[l], g->dir_lo[l]);
+                                                        g->dir[l]);
             ART_TRY(cudaGetLastError());
             g->dir_built[l] = true;
         }
@@ -172,8 +171,7 @@ int prepare_trace(art_grid* g, const art_params* p, bool adjoint)
         double r1 = unit * std::ldexp(1.0, l);
         split_df(r0, lv[l].r0.hi, lv[l].r0.lo);
         split_df(r1, lv[l].rmax.hi, lv[l].rmax.lo);
-        lv[l].dir_hi = g->dir_hi[l];
-        lv[l].dir_lo = g->dir_lo[l];
+        lv[l].dir = g->dir[l];
         lv[l].destroy_w = 1ull << (2 * (lmax_glob - l));
     }
     ART_TRY(cudaMemcpyAsync(g->d_levels, lv, sizeof(lv), cudaMemcpyHostToDevice, g->stream));
@@ -262,7 +260,7 @@ int finish_stats(art_grid* g, art_stats* out)
     out->destroy = d.destroy;
     out->destroy_expected = g->destroy_expected;
     out->L_in = g->last_L_in;
-    out->L_absorbed = d.absorbed;
+    out->L_absorbed = g->last_L_in - d.escaped - d.dropped;
     out->L_escaped = d.escaped;
     out->L_dropped = d.dropped;
     out->level_reached = d.level_reached;
@@ -456,9 +454,10 @@ void art_destroy_grid(art_grid* g)
     dev_free(g->d_levels);
     dev_free(g->d_sched);
     dev_free(g->d_stats);
+    dev_free(g->d_srcL);
+    dev_free(g->d_dL_scratch);
     for (int l = 0; l < kNL; ++l) {
-        dev_free(g->dir_hi[l]);
-        dev_free(g->dir_lo[l]);
+        dev_free(g->dir[l]);
         RayBuf& b = g->buf[l];
         dev_free(b.src); dev_free(b.pix); dev_free(b.L); dev_free(b.tau);
         dev_free(b.parent); dev_free(b.own); dev_free(b.sub);

@@ -87,8 +87,8 @@ struct SrcDev {
 struct LevelInfo {
     df r0;              // start radius of level-l rays (r_max(l-1), 0 at l0), cell units
     df rmax;            // split radius r_max(l), cell units
-    const float4* dir_hi;  // direction table of level l: hi parts (w unused)
-    const float4* dir_lo;  //                              lo parts
+    const float4* dir;     // direction table of level l: 3 float4 per pixel holding
+                           // n (hi, lo) and 1/n (hi, lo) per axis
     unsigned long long destroy_w;  // 4^(l_max_global - l)
 };
 
@@ -100,14 +100,14 @@ struct RayBuf {
     float* tau;
     // adjoint extras (NULL in forward traces)
     unsigned* parent;   // slot of the parent in the level above
-    float* own;         // weighted sum over the ray's own segments (pass 1)
-    float* sub;         // weighted sum over the ray's descendants (filled by the children)
+    double* own;        // weighted sum over the ray's own segments (pass 1)
+    double* sub;        // weighted sum over the ray's descendants (filled by the children)
     unsigned long long cap;
 };
 
 // Per-thread tallies, reduced per block at kernel exit.
 struct Tally {
-    double escaped, dropped, absorbed;
+    double escaped, dropped;
     unsigned long long crossings, destroy;
 };
 
@@ -115,7 +115,7 @@ struct Tally {
 struct DevStats {
     unsigned long long crossings, destroy, rays_total;
     unsigned long long rays_per_level[kNL];
-    double escaped, dropped, absorbed;
+    double escaped, dropped;
     int level_reached;
     int error;
 };
@@ -150,6 +150,7 @@ struct TraceArgs {
     DevStats* stats;
     long long wait_ns;       // bound of a grid-barrier wait (<0: give up at once)
     float gscale;            // adjoint: sigma_H * dx / dV (gamma per unit G)
+    const float* srcL;       // adjoint: source luminosities (gradients scale with them)
 };
 
 enum : int { EV_NONE = 0, EV_EXIT = 1, EV_DROP = 2, EV_SPLIT = 3 };
@@ -159,23 +160,22 @@ enum : int { EV_NONE = 0, EV_EXIT = 1, EV_DROP = 2, EV_SPLIT = 3 };
 // ---------------------------------------------------------------------------------------
 struct Walk {
     df t[3];      // distance from the source to the next face on each axis
-    df dt[3];     // distance between consecutive faces on each axis
+    df d[3];      // distance between consecutive faces on each axis (1/|n_a|)
     df tc;        // distance of the current position
-    df te;        // split radius, or kBig for rays that never split
     int idx;      // linear index of the current cell
     int rem[3];   // cells left on each axis before the ray leaves the grid
-    int stride[3];
     float n[3];   // direction (hi parts) for momentum deposits
     float L, tau;
     float chi;    // opacity of the current cell (prefetched)
 };
 
-// Sets up the walk of a ray of level l with direction n (df) from source position u (df)
-// starting at radius r0. Returns false if the start point lies outside the grid.
-__device__ __forceinline__ bool walk_start(Walk& W, const TraceArgs& A, const df u[3],
-                                           const df n[3], df r0, df te)
+// Sets up the walk of a ray with direction n and reciprocal inv (df, from the direction
+// table) from source position u (df) starting at radius r0. Returns false if the start
+// point lies outside the grid.
+__device__ __forceinline__ bool walk_start(Walk& W, int nx, int ny, int nz, const df u[3],
+                                           const df n[3], const df inv[3], df r0)
 {
-    const int N[3] = {A.nx, A.ny, A.nz};
+    const int N[3] = {nx, ny, nz};
     int c[3];
     bool inside = true;
 #pragma unroll
@@ -187,26 +187,20 @@ __device__ __forceinline__ bool walk_start(Walk& W, const TraceArgs& A, const df
         c[a] = ci;
         inside = inside && ci >= 0 && ci < N[a];
         W.n[a] = n[a].hi;
-        if (n[a].hi > 0.f) {
-            W.rem[a] = N[a] - 1 - ci;
-            W.t[a] = df_div(df_add({(float)(ci + 1), 0.f}, df_neg(u[a])), n[a]);
-            W.dt[a] = df_div({1.f, 0.f}, n[a]);
-        } else if (n[a].hi < 0.f) {
-            W.rem[a] = ci;
-            W.t[a] = df_div(df_add({(float)ci, 0.f}, df_neg(u[a])), n[a]);
-            W.dt[a] = df_div({1.f, 0.f}, df_neg(n[a]));
+        if (n[a].hi != 0.f) {
+            const bool up = n[a].hi > 0.f;
+            W.rem[a] = up ? N[a] - 1 - ci : ci;
+            const df off = df_add({(float)(up ? ci + 1 : ci), 0.f}, df_neg(u[a]));
+            W.t[a] = df_mul(off, inv[a]);
+            W.d[a] = up ? inv[a] : df_neg(inv[a]);
         } else {
             W.rem[a] = 1 << 30;
             W.t[a] = {kBig, 0.f};
-            W.dt[a] = {0.f, 0.f};
+            W.d[a] = {0.f, 0.f};
         }
     }
-    W.stride[0] = W.n[0] > 0.f ? 1 : -1;
-    W.stride[1] = W.n[1] > 0.f ? A.nx : -A.nx;
-    W.stride[2] = W.n[2] > 0.f ? A.nx * A.ny : -(A.nx * A.ny);
     W.tc = r0;
-    W.te = te;
-    W.idx = inside ? c[0] + A.nx * (c[1] + A.ny * c[2]) : 0;
+    W.idx = inside ? c[0] + nx * (c[1] + ny * c[2]) : 0;
     return inside;
 }
 
@@ -217,50 +211,78 @@ struct StepOut {
     float dtau;
     float Lin;
     float G;      // L_in ds phi(dtau)
-    float dL;
+    float dL;     // L_in (1 - e^-dtau)
+    float phi;    // (1 - e^-dtau)/dtau
     int ev;
 };
 
-__device__ __forceinline__ float phi_of(float dtau, float em)
+// (1 - e^-x)/x for x >= 0: Taylor series below 1 (no cancellation), exponential above.
+__device__ __forceinline__ float phi_of(float x)
 {
-    // (1 - e^-x)/x from em = expm1(-x); series below 1e-4
-    return dtau > 1e-4f ? __fdividef(-em, dtau)
-                        : fmaf(dtau, fmaf(dtau, 1.f / 6.f, -0.5f), 1.f);
+    if (x < 1.f) {
+        float r = -1.f / 479001600.f;          // -1/12!
+        r = fmaf(r, x, 1.f / 39916800.f);
+        r = fmaf(r, x, -1.f / 3628800.f);
+        r = fmaf(r, x, 1.f / 362880.f);
+        r = fmaf(r, x, -1.f / 40320.f);
+        r = fmaf(r, x, 1.f / 5040.f);
+        r = fmaf(r, x, -1.f / 720.f);
+        r = fmaf(r, x, 1.f / 120.f);
+        r = fmaf(r, x, -1.f / 24.f);
+        r = fmaf(r, x, 1.f / 6.f);
+        r = fmaf(r, x, -0.5f);
+        return fmaf(r, x, 1.f);
+    }
+    return __fdividef(1.f - __expf(-x), x);
 }
 
-// One step of the walk: the segment from tc to the next face or the split radius.
+// Advances axis a (compile-time index) by one face.
+template <int a>
+__device__ __forceinline__ void walk_advance(Walk& W)
+{
+    W.rem[a] -= 1;
+    W.t[a] = df_add(W.t[a], W.d[a]);
+}
+
+// One step of the walk: the segment from tc to the next face or to the split radius rmax
+// (when the ray splits at all).
 template <bool kCountOnly>
-__device__ __forceinline__ StepOut walk_step(Walk& W, const float* __restrict__ chi_arr,
-                                             float tau_max)
+__device__ __forceinline__ StepOut walk_step(Walk& W, bool splits, df rmax, int sy, int sz,
+                                             const float* __restrict__ chi_arr, float tau_max)
 {
     StepOut o;
-    // earliest face crossing (lexicographic on the normalised df values)
-    bool l01 = df_le(W.t[0], W.t[1]);
-    df t01 = l01 ? W.t[0] : W.t[1];
-    bool l2 = df_le(t01, W.t[2]);
-    df tm = l2 ? t01 : W.t[2];
-    bool split = df_le(W.te, tm);
-    df tend = split ? W.te : tm;
+    // earliest face crossing (lexicographic order of the normalised df values)
+    const bool c01 = df_le(W.t[0], W.t[1]);
+    df tm = c01 ? W.t[0] : W.t[1];
+    int a = c01 ? 0 : 1;
+    if (!df_le(tm, W.t[2])) {
+        tm = W.t[2];
+        a = 2;
+    }
+    const bool split = splits && df_le(rmax, tm);
+    const df tend = split ? rmax : tm;
     o.ds = df_diff(tend, W.tc);
-    // axes that cross together with the earliest one (relative tie 1e-12)
+    // axes crossing together with the earliest one (relative tie 1e-12): a diagonal step
     const float tol = 1e-12f * tm.hi;
-    int mask = 0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-        if (df_diff(W.t[a], tm) <= tol) mask |= 1 << a;
-    // next cell, and prefetch of its opacity
+    const int mask = (df_diff(W.t[0], tm) <= tol ? 1 : 0) | (df_diff(W.t[1], tm) <= tol ? 2 : 0) |
+                     (df_diff(W.t[2], tm) <= tol ? 4 : 0);
+    const bool single = mask == (1 << a);
+    // next cell and whether it leaves the grid
     int nidx = W.idx;
     bool out = false;
-    if (!split) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            if (mask & (1 << a)) {
-                nidx += W.stride[a];
-                out = out || (W.rem[a] == 0);
-            }
+    if (single) {
+        const int r = a == 0 ? W.rem[0] : (a == 1 ? W.rem[1] : W.rem[2]);
+        const float na = a == 0 ? W.n[0] : (a == 1 ? W.n[1] : W.n[2]);
+        const int st = a == 0 ? 1 : (a == 1 ? sy : sz);
+        out = r == 0;
+        nidx += na > 0.f ? st : -st;
+    } else {
+        if (mask & 1) { out = out || W.rem[0] == 0; nidx += W.n[0] > 0.f ? 1 : -1; }
+        if (mask & 2) { out = out || W.rem[1] == 0; nidx += W.n[1] > 0.f ? sy : -sy; }
+        if (mask & 4) { out = out || W.rem[2] == 0; nidx += W.n[2] > 0.f ? sz : -sz; }
     }
     float nchi = 0.f;
-    if (!split && !out) nchi = __ldg(chi_arr + nidx);
+    if (!split && !out) nchi = __ldg(chi_arr + nidx);  // prefetch for the next step
     // deposit in the current cell
     o.cell = -1;
     o.ev = EV_NONE;
@@ -268,17 +290,19 @@ __device__ __forceinline__ StepOut walk_step(Walk& W, const float* __restrict__ 
     o.G = 0.f;
     o.dL = 0.f;
     o.dtau = 0.f;
+    o.phi = 1.f;
     if (o.ds > 0.f) {
         o.cell = W.idx;
-        float dtau = W.chi * o.ds;
-        o.dtau = dtau;
+        const float x = W.chi * o.ds;
+        o.dtau = x;
         if (!kCountOnly) {
-            float em = expm1f(-dtau);
-            o.dL = -W.L * em;
-            o.G = W.L * o.ds * phi_of(dtau, em);
+            const float ph = phi_of(x);
+            o.phi = ph;
+            o.G = W.L * o.ds * ph;
+            o.dL = W.L * x * ph;
             W.L = W.L - o.dL;
         }
-        W.tau += dtau;
+        W.tau += x;
         if (W.tau > tau_max) o.ev = EV_DROP;
     }
     if (o.ev == EV_NONE) {
@@ -287,12 +311,15 @@ __device__ __forceinline__ StepOut walk_step(Walk& W, const float* __restrict__ 
         } else if (out) {
             o.ev = EV_EXIT;
         } else {
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-                if (mask & (1 << a)) {
-                    W.rem[a] -= 1;
-                    W.t[a] = df_add(W.t[a], W.dt[a]);
-                }
+            if (single) {
+                if (a == 0) walk_advance<0>(W);
+                else if (a == 1) walk_advance<1>(W);
+                else walk_advance<2>(W);
+            } else {
+                if (mask & 1) walk_advance<0>(W);
+                if (mask & 2) walk_advance<1>(W);
+                if (mask & 4) walk_advance<2>(W);
+            }
             W.tc = tm;
             W.idx = nidx;
             W.chi = nchi;
@@ -332,6 +359,105 @@ __device__ __forceinline__ void deposit_warp(float4* __restrict__ acc, int cell,
                      "f"(v.y), "f"(v.z), "f"(v.w)
                      : "memory");
     }
+}
+
+// ---------------------------------------------------------------------------------------
+// helpers shared by the forward and backward kernels
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void tally_flush(const Tally& T, DevStats* st)
+{
+    __shared__ double s_d[2];
+    __shared__ unsigned long long s_u[2];
+    if (threadIdx.x == 0) { s_d[0] = s_d[1] = 0.0; s_u[0] = s_u[1] = 0ull; }
+    __syncthreads();
+    double e = T.escaped, d = T.dropped;
+    unsigned long long c = T.crossings, w = T.destroy;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        e += __shfl_down_sync(kFull, e, off);
+        d += __shfl_down_sync(kFull, d, off);
+        c += __shfl_down_sync(kFull, c, off);
+        w += __shfl_down_sync(kFull, w, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&s_d[0], e); atomicAdd(&s_d[1], d);
+        atomicAdd(&s_u[0], c); atomicAdd(&s_u[1], w);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&st->escaped, s_d[0]);
+        atomicAdd(&st->dropped, s_d[1]);
+        atomicAdd(&st->crossings, s_u[0]);
+        atomicAdd(&st->destroy, s_u[1]);
+    }
+}
+
+// Starts the walk of ray i of level l: loads its record, its source and its direction
+// entry. Returns true if the ray starts inside the grid. L0 receives its entering L.
+__device__ __forceinline__ bool ray_begin(const TraceArgs& A, const LevelInfo& LV, const RayBuf& B,
+                                          int l, unsigned long long i, Walk& W, unsigned& s,
+                                          unsigned& p, float& L0, bool& splits)
+{
+    s = __ldcg(B.src + i);
+    p = __ldcg(B.pix + i);
+    const float4 sh = __ldg(&A.src[s].hi);
+    const float4 sl = __ldg(&A.src[s].lo);
+    L0 = (l == A.level0) ? sh.w : __ldcg(B.L + i);
+    const float tau0 = (l == A.level0) ? 0.f : __ldcg(B.tau + i);
+    splits = l < __float_as_int(sl.w);
+    const float4 e0 = __ldg(LV.dir + 3ull * p);
+    const float4 e1 = __ldg(LV.dir + 3ull * p + 1);
+    const float4 e2 = __ldg(LV.dir + 3ull * p + 2);
+    const df u[3] = {{sh.x, sl.x}, {sh.y, sl.y}, {sh.z, sl.z}};
+    const df n[3] = {{e0.x, e0.w}, {e0.y, e1.x}, {e0.z, e1.y}};
+    const df inv[3] = {{e1.z, e2.y}, {e1.w, e2.z}, {e2.x, e2.w}};
+    const bool inside = walk_start(W, A.nx, A.ny, A.nz, u, n, inv, LV.r0);
+    W.L = L0;
+    W.tau = tau0;
+    W.chi = inside ? __ldg(A.chi + W.idx) : 0.f;
+    return inside;
+}
+
+// Grid-wide barrier for a cooperative launch. Every wait is bounded by wait_ns of
+// %globaltimer; on expiry the block records ART_ETIMEOUT and the barrier returns false.
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool grid_barrier(Sched* sc, DevStats* st, long long wait_ns)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned* gen = &sc->bar_gen;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&sc->bar_count, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            atomicExch(&sc->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&sc->bar_gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*gen == g) {
+                if (wait_ns < 0 || (long long)(global_ns() - t0) > wait_ns) {
+                    atomicCAS(&st->error, 0, -4);  // ART_ETIMEOUT
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(200);
+            }
+        }
+        __threadfence();
+        if (*((volatile int*)&st->error) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
 }
 
 }  // namespace art

@@ -32,8 +32,7 @@ struct art_grid {
     art::DevStats* d_stats = nullptr;
     art::DevStats* h_stats = nullptr;  // pinned
 
-    float4* dir_hi[art::kNL] = {};
-    float4* dir_lo[art::kNL] = {};
+    float4* dir[art::kNL] = {};     // per level: 3 float4 per pixel (n and 1/n as df)
     bool dir_built[art::kNL] = {};
     bool dir_rotate = false;
     double dir_rot[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
@@ -43,8 +42,11 @@ struct art_grid {
     unsigned long long buf_cap_req[art::kNL] = {};
     bool buf_adj[art::kNL] = {};                     // adjoint arrays allocated
 
-    // adjoint scratch
-    float* d_tmp_grad = nullptr;
+    // adjoint: source luminosities and a dL buffer for callers that pass none
+    float* d_srcL = nullptr;
+    double* d_dL_scratch = nullptr;
+    size_t srcL_cap = 0;
+    std::vector<float> h_srcL;
 
     int lmax_glob = 0;
     int last_lmax = 0;

@@ -53,7 +53,7 @@ __device__ __forceinline__ void cossin_pi_frac(long long num, long long den, dou
 
 __global__ void k_directions(int level, unsigned long long npix, double r0, double r1, double r2,
                              double r3, double r4, double r5, double r6, double r7, double r8,
-                             int rotate, float4* __restrict__ hi, float4* __restrict__ lo)
+                             int rotate, float4* __restrict__ dir)
 {
     unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
     if (p >= npix) return;
@@ -93,15 +93,20 @@ __global__ void k_directions(int level, unsigned long long npix, double r0, doub
     } else {
         w[0] = v[0]; w[1] = v[1]; w[2] = v[2];
     }
-    float h[3], l[3];
+    float h[3], l[3], ih[3], il[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (fabs(w[a]) < 5.9604644775390625e-08) w[a] = 0.0;  // 2^-24
         h[a] = __double2float_rn(w[a]);
         l[a] = __double2float_rn(w[a] - (double)h[a]);
+        const double iv = w[a] != 0.0 ? 1.0 / w[a] : 0.0;
+        ih[a] = __double2float_rn(iv);
+        il[a] = __double2float_rn(iv - (double)ih[a]);
     }
-    hi[p] = make_float4(h[0], h[1], h[2], 0.f);
-    lo[p] = make_float4(l[0], l[1], l[2], 0.f);
+    // layout: {n_hx, n_hy, n_hz, n_lx}, {n_ly, n_lz, i_hx, i_hy}, {i_hz, i_lx, i_ly, i_lz}
+    dir[3 * p] = make_float4(h[0], h[1], h[2], l[0]);
+    dir[3 * p + 1] = make_float4(l[1], l[2], ih[0], ih[1]);
+    dir[3 * p + 2] = make_float4(ih[2], il[0], il[1], il[2]);
 }
 
 // chi per cell length (dx) in FP32 from the density fields; flags bad densities.
@@ -139,63 +144,10 @@ __global__ void k_inject(int s0, int nsrc, unsigned npix0, RayBuf B, unsigned lo
     B.tau[i] = 0.f;
 }
 
-__device__ __forceinline__ void tally_flush(const Tally& T, DevStats* st)
-{
-    __shared__ double s_d[3];
-    __shared__ unsigned long long s_u[2];
-    if (threadIdx.x == 0) { s_d[0] = s_d[1] = s_d[2] = 0.0; s_u[0] = s_u[1] = 0ull; }
-    __syncthreads();
-    double e = T.escaped, d = T.dropped, a = T.absorbed;
-    unsigned long long c = T.crossings, w = T.destroy;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        e += __shfl_down_sync(kFull, e, off);
-        d += __shfl_down_sync(kFull, d, off);
-        a += __shfl_down_sync(kFull, a, off);
-        c += __shfl_down_sync(kFull, c, off);
-        w += __shfl_down_sync(kFull, w, off);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&s_d[0], e); atomicAdd(&s_d[1], d); atomicAdd(&s_d[2], a);
-        atomicAdd(&s_u[0], c); atomicAdd(&s_u[1], w);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        atomicAdd(&st->escaped, s_d[0]);
-        atomicAdd(&st->dropped, s_d[1]);
-        atomicAdd(&st->absorbed, s_d[2]);
-        atomicAdd(&st->crossings, s_u[0]);
-        atomicAdd(&st->destroy, s_u[1]);
-    }
-}
-
-// Starts the walk of ray i of level l. Returns true if the ray is inside the grid.
-__device__ __forceinline__ bool ray_begin(const TraceArgs& A, const LevelInfo& LV, const RayBuf& B,
-                                          int l, unsigned long long i, Walk& W, unsigned& s,
-                                          unsigned& p, float& L0, bool& splits)
-{
-    s = __ldcg(B.src + i);
-    p = __ldcg(B.pix + i);
-    const float4 sh = __ldg(&A.src[s].hi);
-    const float4 sl = __ldg(&A.src[s].lo);
-    L0 = (l == A.level0) ? sh.w : __ldcg(B.L + i);
-    const float tau0 = (l == A.level0) ? 0.f : __ldcg(B.tau + i);
-    const int lmax_s = __float_as_int(sl.w);
-    splits = l < lmax_s;
-    const float4 dh = __ldg(LV.dir_hi + p);
-    const float4 dl = __ldg(LV.dir_lo + p);
-    const df u[3] = {{sh.x, sl.x}, {sh.y, sl.y}, {sh.z, sl.z}};
-    const df n[3] = {{dh.x, dl.x}, {dh.y, dl.y}, {dh.z, dl.z}};
-    const df te = splits ? LV.rmax : df{kBig, 0.f};
-    bool inside = walk_start(W, A, u, n, LV.r0, te);
-    W.L = L0;
-    W.tau = tau0;
-    W.chi = inside ? __ldg(A.chi + W.idx) : 0.f;
-    return inside;
-}
-
 // Processes rays [cursor .. end) of level l (cursor advanced atomically by warps, `chunk`
-// rays at a time). Warp-uniform: every lane of the warp must call it.
+// rays at a time). Idle lanes are refilled once at least a quarter of the warp is idle, so
+// the ray set-up runs with many lanes at once. Warp-uniform: every lane of the warp must
+// call it.
 __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
                          unsigned long long end, Tally& T)
 {
@@ -205,6 +157,7 @@ __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
     const RayBuf B = A.buf[l];
     const RayBuf C = A.buf[l + 1];
     unsigned long long* child_count = &A.sched->count[l + 1];
+    const int sy = A.nx, sz = A.nx * A.ny;
 
     unsigned long long wnext = 0, wend = 0;
     bool more = true;
@@ -218,30 +171,34 @@ __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
     for (;;) {
         // refill idle lanes from the warp's chunk, fetching chunks as needed
         unsigned need = __ballot_sync(kFull, !active);
-        while (need && more) {
-            if (wnext >= wend) {
-                unsigned long long b = 0;
-                if (lane == 0) b = atomicAdd(cursor, (unsigned long long)A.chunk);
-                b = __shfl_sync(kFull, b, 0);
-                if (b >= end) { more = false; break; }
-                wnext = b;
-                wend = min(b + (unsigned long long)A.chunk, end);
-            }
-            const unsigned avail = (unsigned)min(wend - wnext, 32ull);
-            const unsigned rank = __popc(need & lt);
-            if (!active && rank < avail) {
-                bool inside = ray_begin(A, LV, B, l, wnext + rank, W, s, p, L0, splits);
-                if (inside) {
-                    active = true;
-                } else {  // starts outside the grid: escapes with its full luminosity
-                    T.escaped += (double)L0;
-                    T.destroy += LV.destroy_w;
+        if (__popc(need) >= 8 || need == kFull) {
+            while (need && more) {
+                if (wnext >= wend) {
+                    unsigned long long b = 0;
+                    if (lane == 0) b = atomicAdd(cursor, (unsigned long long)A.chunk);
+                    b = __shfl_sync(kFull, b, 0);
+                    if (b >= end) { more = false; break; }
+                    wnext = b;
+                    wend = min(b + (unsigned long long)A.chunk, end);
                 }
+                const unsigned avail = (unsigned)min(wend - wnext, 32ull);
+                const unsigned rank = __popc(need & lt);
+                if (!active && rank < avail) {
+                    if (ray_begin(A, LV, B, l, wnext + rank, W, s, p, L0, splits)) {
+                        active = true;
+                    } else {  // starts outside the grid: escapes with its full luminosity
+                        T.escaped += (double)L0;
+                        T.destroy += LV.destroy_w;
+                    }
+                }
+                wnext += min(avail, (unsigned)__popc(need));
+                need = __ballot_sync(kFull, !active);
             }
-            wnext += min(avail, (unsigned)__popc(need));
-            need = __ballot_sync(kFull, !active);
         }
-        if (!__any_sync(kFull, active)) break;
+        if (!__any_sync(kFull, active)) {
+            if (!more) break;
+            continue;
+        }
 
         bool want_split = false;
 #pragma unroll 1
@@ -249,7 +206,7 @@ __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
             int cell = -1;
             float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
             if (active) {
-                StepOut o = walk_step<false>(W, A.chi, A.tau_max);
+                const StepOut o = walk_step<false>(W, splits, LV.rmax, sy, sz, A.chi, A.tau_max);
                 if (o.cell >= 0) {
                     cell = o.cell;
                     dv = make_float4(o.G, o.dL * W.n[0], o.dL * W.n[1], o.dL * W.n[2]);
@@ -257,7 +214,6 @@ __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
                 }
                 if (o.ev != EV_NONE) {
                     active = false;
-                    T.absorbed += (double)L0 - (double)W.L;
                     if (o.ev == EV_SPLIT) {
                         want_split = true;
                     } else {
@@ -298,7 +254,7 @@ __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
 // Plain schedule: all rays of level l currently in its buffer.
 __global__ void k_trace_level(const __grid_constant__ TraceArgs A, int l)
 {
-    Tally T = {0.0, 0.0, 0.0, 0ull, 0ull};
+    Tally T = {0.0, 0.0, 0ull, 0ull};
     // a front that overflowed (status set by the writer) is cut at the buffer capacity
     const unsigned long long end =
         min(*((volatile unsigned long long*)&A.sched->count[l]), A.buf[l].cap);
@@ -318,52 +274,10 @@ __global__ void k_reset_counts(Sched* sc)
     if (t < kNL) { sc->count[t] = 0; sc->cursor[t] = 0; }
 }
 
-// Grid-wide barrier for a cooperative launch. Every wait is bounded by wait_ns of
-// %globaltimer; on expiry the block records ART_ETIMEOUT and the barrier returns false.
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ bool grid_barrier(Sched* sc, DevStats* st, long long wait_ns)
-{
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        volatile unsigned* gen = &sc->bar_gen;
-        const unsigned g = *gen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(&sc->bar_count, 1u) + 1u;
-        if (arrived == gridDim.x) {
-            atomicExch(&sc->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&sc->bar_gen, 1u);
-        } else {
-            const unsigned long long t0 = global_ns();
-            while (*gen == g) {
-                if (wait_ns < 0 || (long long)(global_ns() - t0) > wait_ns) {
-                    atomicCAS(&st->error, 0, -4);  // ART_ETIMEOUT
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(200);
-            }
-        }
-        __threadfence();
-        if (*((volatile int*)&st->error) != 0) ok = 0;
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
 // Persistent schedule: all sources, all levels, one cooperative launch.
 __global__ void k_trace_persistent(const __grid_constant__ TraceArgs A)
 {
-    Tally T = {0.0, 0.0, 0.0, 0ull, 0ull};
+    Tally T = {0.0, 0.0, 0ull, 0ull};
     Sched* sc = A.sched;
     __shared__ int s_level;
     __shared__ unsigned long long s_end;

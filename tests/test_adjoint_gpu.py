@@ -1,0 +1,94 @@
+"""GPU adjoint (art_trace_backward / ARTFunction) vs the oracle's reverse sweep, which the
+CPU suite pins to FP64 finite differences."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_1711_06277_gb300 import synth
+from tests import parity as PA
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def art():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1711_06277_gb300 import art as A
+    return A
+
+
+def _case(A, n, nsrc, seed, sigma_ln=1.5, tau_box=10.0, level0=4, nH_scale=None,
+          schedule="persistent"):
+    rho = synth.lognormal_field(n, sigma_ln, seed=seed).astype(np.float32)
+    pos = synth.uniform_positions(nsrc, seed=seed)
+    L = synth.power_law_luminosities(nsrc, seed=seed)
+    w = synth.uniform_weights(n, seed=seed).astype(np.float32)
+    p = A.Params(level0=level0, tau_max=30.0, sigma_H=tau_box, schedule=schedule)
+    nH = None if nH_scale is None else (nH_scale * rho).astype(np.float32)
+    if nH is not None:
+        p.sigma_d = 3.0
+    dev = torch.device("cuda")
+    g = A.Grid(torch.from_numpy(rho).to(dev), 1.0 / n,
+               nH=None if nH is None else torch.from_numpy(nH).to(dev))
+    g.add_sources(pos, L)
+    fwd = g.trace(p, force=False)
+    grad, dL, st = g.trace_backward(p, torch.from_numpy(w).to(dev))
+    loss = float((w.astype(np.float64) * fwd["gamma"].cpu().numpy()).sum())
+    out = dict(grad=grad.cpu().numpy(), dL=dL.cpu().numpy(), stats=st, loss=loss,
+               fstats=fwd["stats"])
+    g.close()
+    prob = O.Problem(nH0=rho, pos=pos, L=L, dx=1.0 / n, nH=nH, sigma_H=p.sigma_H,
+                     sigma_d=p.sigma_d, level0=level0, tau_max=30.0)
+    rg, rdL, rloss = O.trace_adjoint(prob, w, nthreads=8)
+    return out, (rg, rdL, rloss), L
+
+
+def _check(out, ref, L):
+    rg, rdL, rloss = ref
+    assert out["stats"]["status"] == 0
+    assert out["stats"]["destroy"] == out["stats"]["destroy_expected"]
+    assert out["stats"]["crossings"] == out["fstats"]["crossings"]
+    PA.compare_field(out["grad"], rg, what="dloss/dlog nH0")
+    np.testing.assert_allclose(out["dL"], rdL, rtol=PA.REL)
+    # the loss is linear in every L_s: sum_s L_s dloss/dL_s = loss
+    assert float((L * out["dL"]).sum()) == pytest.approx(rloss, rel=PA.REL)
+    assert out["loss"] == pytest.approx(rloss, rel=PA.REL)
+
+
+def test_adjoint_32_fd_subcase(art):
+    out, ref, L = _case(art, 32, 4, seed=4)
+    _check(out, ref, L)
+
+
+def test_adjoint_config4_128_16src(art):
+    out, ref, L = _case(art, 128, 16, seed=4)
+    _check(out, ref, L)
+
+
+def test_adjoint_with_dust_and_deep_levels(art):
+    out, ref, L = _case(art, 48, 3, seed=8, level0=1, nH_scale=1.3)
+    _check(out, ref, L)
+
+
+def test_autograd_function_matches_backward(art):
+    n = 32
+    rho = synth.lognormal_field(n, 1.5, seed=2).astype(np.float32)
+    pos = synth.uniform_positions(3, seed=2)
+    L = synth.power_law_luminosities(3, seed=2)
+    w = torch.from_numpy(synth.uniform_weights(n, seed=2).astype(np.float32)).cuda()
+    p = art.Params(level0=3, tau_max=30.0, sigma_H=8.0)
+    logn = torch.log(torch.from_numpy(rho).cuda()).requires_grad_(True)
+    Lt = torch.tensor(L, dtype=torch.float64, requires_grad=True)
+    g = art.Grid(torch.from_numpy(rho).cuda(), 1.0 / n)
+    gamma = art.ARTFunction.apply(logn, Lt, g, p, pos)
+    loss = (gamma.double() * w.double()).sum()
+    loss.backward()
+    prob = O.Problem(nH0=np.exp(np.log(rho)), pos=pos, L=L, dx=1.0 / n, sigma_H=8.0, level0=3,
+                     tau_max=30.0)
+    rg, rdL, rloss = O.trace_adjoint(prob, w.cpu().numpy(), nthreads=8)
+    PA.compare_field(logn.grad.cpu().numpy(), rg, rel=3e-5, what="autograd grad")
+    np.testing.assert_allclose(Lt.grad.numpy(), rdL, rtol=PA.REL)
+    g.close()
