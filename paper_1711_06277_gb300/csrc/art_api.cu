@@ -132,8 +132,18 @@ int prepare_trace(art_grid* g, const art_params* p, bool adjoint)
         if (rc) return rc;
         g->src_cap = ns;
     }
-    ART_TRY(cudaMemcpyAsync(g->d_src, hs.data(), ns * sizeof(SrcDev), cudaMemcpyHostToDevice,
-                            g->stream));
+    // uploads only when the sources or the parameters that shape the tables changed, so an
+    // unchanged trace enqueues no host-to-device copy (and can be captured in a CUDA graph)
+    const bool same = g->prep_valid && g->prep_version == g->src_version &&
+                      g->prep_level0 == l0 && g->prep_level_max == p->level_max &&
+                      g->prep_m_ray == p->m_ray && g->prep_adjoint == adjoint &&
+                      g->prep_schedule == p->schedule && g->prep_qcap == p->queue_capacity;
+    if (!same) {
+        g->h_src_stage.assign(hs.data(), hs.data() + hs.size());
+        if (!g->h_src_stage.data()) return ART_ENOMEM;
+        ART_TRY(cudaMemcpyAsync(g->d_src, g->h_src_stage.data(), ns * sizeof(SrcDev),
+                                cudaMemcpyHostToDevice, g->stream));
+    }
     g->lmax_glob = lmax_glob;
     // --- direction tables (FP64 HEALPix, rotated), rebuilt when the rotation changes
     const bool rotate = (p->flags & ART_F_ROTATE) != 0;
@@ -174,7 +184,11 @@ int prepare_trace(art_grid* g, const art_params* p, bool adjoint)
         lv[l].dir = g->dir[l];
         lv[l].destroy_w = 1ull << (2 * (lmax_glob - l));
     }
-    ART_TRY(cudaMemcpyAsync(g->d_levels, lv, sizeof(lv), cudaMemcpyHostToDevice, g->stream));
+    if (!same || std::memcmp(lv, g->h_levels, sizeof(lv)) != 0) {
+        std::memcpy(g->h_levels, lv, sizeof(lv));
+        ART_TRY(cudaMemcpyAsync(g->d_levels, g->h_levels, sizeof(lv), cudaMemcpyHostToDevice,
+                                g->stream));
+    }
     // --- ray buffers: level l0 holds every base ray of the batch; deeper levels hold at
     // most the queue capacity (persistent) or one source's whole front (plain)
     const bool plain = p->schedule == ART_SCHED_PLAIN;
@@ -215,6 +229,14 @@ int prepare_trace(art_grid* g, const art_params* p, bool adjoint)
         keep.cap = 0;
         g->buf[l] = keep;
     }
+    g->prep_valid = true;
+    g->prep_version = g->src_version;
+    g->prep_level0 = l0;
+    g->prep_level_max = p->level_max;
+    g->prep_m_ray = p->m_ray;
+    g->prep_adjoint = adjoint;
+    g->prep_schedule = p->schedule;
+    g->prep_qcap = p->queue_capacity;
     // --- opacity per cell length
     const double sH_dx = p->sigma_H * g->dx;
     const double sd_dx = g->nH ? p->sigma_d * g->dx : 0.0;
@@ -323,6 +345,7 @@ int art_create_grid(art_grid** out, int nx, int ny, int nz, const double box_lo[
     if (!rc) rc = dev_alloc(&g->d_sched, 1);
     if (!rc) rc = dev_alloc(&g->d_stats, 1);
     if (!rc) rc = cuda_status(cudaMallocHost((void**)&g->h_stats, sizeof(DevStats)));
+    if (!rc) rc = cuda_status(cudaMallocHost((void**)&g->h_levels, sizeof(LevelInfo) * kNL));
     if (rc) {
         art_destroy_grid(g);
         return rc;
@@ -352,6 +375,7 @@ int art_add_sources(art_grid* g, int n, const double* h_pos, const double* h_L)
     }
     g->pos.insert(g->pos.end(), h_pos, h_pos + 3 * (size_t)n);
     g->L.insert(g->L.end(), h_L, h_L + (size_t)n);
+    g->src_version += 1;
     return ART_OK;
 }
 
@@ -360,6 +384,7 @@ int art_clear_sources(art_grid* g)
     if (!g) return ART_EINVAL;
     g->pos.clear();
     g->L.clear();
+    g->src_version += 1;
     return ART_OK;
 }
 
@@ -463,6 +488,7 @@ void art_destroy_grid(art_grid* g)
         dev_free(b.parent); dev_free(b.own); dev_free(b.sub);
     }
     if (g->h_stats) cudaFreeHost(g->h_stats);
+    if (g->h_levels) cudaFreeHost(g->h_levels);
     delete g;
 }
 

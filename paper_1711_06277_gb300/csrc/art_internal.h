@@ -8,6 +8,28 @@
 #include "art.h"
 #include "art_device.cuh"
 
+// A growable array in pinned host memory (copies from it can be captured in a graph).
+template <class T>
+struct PinnedVec {
+    T* data_ = nullptr;
+    size_t n_ = 0, cap_ = 0;
+    ~PinnedVec() { if (data_) cudaFreeHost(data_); }
+    T* data() { return data_; }
+    void assign(const T* b, const T* e)
+    {
+        size_t n = (size_t)(e - b);
+        if (n > cap_) {
+            if (data_) cudaFreeHost(data_);
+            data_ = nullptr;
+            cap_ = 0;
+            if (cudaMallocHost((void**)&data_, n * sizeof(T)) != cudaSuccess) { data_ = nullptr; n_ = 0; return; }
+            cap_ = n;
+        }
+        for (size_t i = 0; i < n; ++i) data_[i] = b[i];
+        n_ = n;
+    }
+};
+
 struct art_grid {
     int device = 0;
     int sms = 1;
@@ -47,6 +69,16 @@ struct art_grid {
     double* d_dL_scratch = nullptr;
     size_t srcL_cap = 0;
     std::vector<float> h_srcL;
+
+    // what the device copies of the source table and level constants were built from
+    art::LevelInfo* h_levels = nullptr;          // pinned staging of the level constants
+    PinnedVec<art::SrcDev> h_src_stage;          // pinned staging of the source table
+    unsigned long long src_version = 0;
+    unsigned long long prep_version = 0;
+    bool prep_valid = false, prep_adjoint = false;
+    int prep_level0 = -1, prep_level_max = -2, prep_schedule = -1;
+    double prep_m_ray = 0.0;
+    long long prep_qcap = -1;
 
     int lmax_glob = 0;
     int last_lmax = 0;
