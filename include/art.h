@@ -169,6 +169,29 @@ int art_dt_substep(void* stream, long long ncell, const float* d_gamma, const fl
                    const float* d_xn, double alpha_B, double C, void* d_scratch, double* d_dt);
 long long art_dt_scratch_bytes(long long ncell);
 
+/* Largest ncell accepted by art_dt_substep_static. */
+#define ART_DT_STATIC_MAX_CELLS (1ll << 24)
+
+/* The substep size of art_dt_substep, for callers that cannot allocate device memory (the
+ * paper has no counterpart): the same result, with the per-block partial minima held in a
+ * fixed array inside the library (256 KB, one float per 256-cell tile) instead of caller
+ * scratch. Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.
+ * d_gamma, d_nH, d_xn: device, ncell floats each (read); d_dt: device, 1 double (written).
+ * Limits and sharing:
+ *   - ncell must be in 1..ART_DT_STATIC_MAX_CELLS (2^24); larger inputs return ART_EINVAL
+ *     with nothing enqueued;
+ *   - the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call before any
+ *     stream capture;
+ *   - every call on a device shares the one array, which keeps the last call's partials;
+ *     each call writes every partial it reads, so no clearing is needed, but calls whose
+ *     GPU work overlaps (different streams, no ordering between them) race and give wrong
+ *     results: order them on one stream or with events.
+ * Errors: ART_EINVAL, ART_ECUDA. */
+int art_dt_substep_static(void* stream, long long ncell, const float* d_gamma,
+                          const float* d_nH, const float* d_xn, double alpha_B, double C,
+                          double* d_dt);
+
 /* Frees the grid and everything it allocated (not the borrowed fields). NULL is a no-op. */
 void art_destroy_grid(art_grid* g);
 

@@ -27,9 +27,10 @@ ART_F_ROTATE = 1
 EXPORTED = [
     "art_params_default", "art_create_grid", "art_update_fields", "art_add_sources",
     "art_clear_sources", "art_num_sources", "art_trace", "art_get_stats", "art_trace_backward",
-    "art_xn_update", "art_dt_substep", "art_dt_scratch_bytes", "art_destroy_grid",
-    "art_strerror",
+    "art_xn_update", "art_dt_substep", "art_dt_scratch_bytes", "art_dt_substep_static",
+    "art_destroy_grid", "art_strerror",
 ]
+ART_DT_STATIC_MAX_CELLS = 1 << 24
 
 
 class ArtParams(ctypes.Structure):
@@ -116,6 +117,8 @@ def lib():
         L.art_dt_substep.restype = i
         L.art_dt_scratch_bytes.argtypes = [ll]
         L.art_dt_scratch_bytes.restype = ll
+        L.art_dt_substep_static.argtypes = [vp, ll, vp, vp, vp, d, d, vp]
+        L.art_dt_substep_static.restype = i
         L.art_destroy_grid.argtypes = [vp]
         L.art_destroy_grid.restype = None
         L.art_strerror.argtypes = [i]

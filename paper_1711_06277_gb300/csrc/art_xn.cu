@@ -2,6 +2,7 @@
 // size of Eq. e:dtss, elementwise over cells.
 #include <cfloat>
 #include <cmath>
+#include <mutex>
 
 #include "art.h"
 
@@ -95,6 +96,43 @@ constexpr int kDtBlocks = 1024;
 
 }  // namespace
 
+// ---------------------------------------------------------------------------------------
+// Allocation-free variant of art_dt_substep (no counterpart in the paper).
+//
+// Some callers cannot call cudaMalloc: code embedded in a host framework that owns all of
+// the device memory through its own pool, where a fresh allocation fails or fragments that
+// pool, and latency-critical loops that cannot afford the implicit device synchronization of
+// cudaMalloc/cudaFree. For them the per-block partial minima live in this fixed array,
+// which every GPU that loads the library keeps for the life of the process: one float per
+// 256-cell tile, so inputs of up to ART_DT_STATIC_MAX_CELLS cells.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+constexpr int kStaticTiles = 65536;  // ART_DT_STATIC_MAX_CELLS / 256
+static __device__ __align__(256) float g_dt_partials[kStaticTiles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+float* g_static_ptr[kMaxDevices] = {};
+
+// Device address of g_dt_partials on the current device, looked up once per device. In
+// host code the symbol's name is only a host-side stand-in and must never reach a kernel.
+int static_partials(float** out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ART_ECUDA;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_dt_partials) != cudaSuccess || !p) return ART_ECUDA;
+        g_static_ptr[dev] = static_cast<float*>(p);
+    }
+    *out = g_static_ptr[dev];
+    return ART_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int art_xn_update(void* stream, long long ncell, const float* d_gamma, const float* d_nH,
@@ -127,6 +165,24 @@ int art_dt_substep(void* stream, long long ncell, const float* d_gamma, const fl
     k_dt_partial<<<blocks, 256, 0, s>>>(ncell, d_gamma, d_nH, d_xn, (float)alpha_B,
                                         (float*)d_scratch);
     k_dt_final<<<1, 1024, 0, s>>>(blocks, (const float*)d_scratch, C, d_dt);
+    return cudaGetLastError() == cudaSuccess ? ART_OK : ART_ECUDA;
+}
+
+int art_dt_substep_static(void* stream, long long ncell, const float* d_gamma, const float* d_nH,
+                          const float* d_xn, double alpha_B, double C, double* d_dt)
+{
+    if (ncell <= 0 || !d_gamma || !d_nH || !d_xn || !d_dt) return ART_EINVAL;
+    if (ncell > ART_DT_STATIC_MAX_CELLS) return ART_EINVAL;  // beyond the fixed scratch
+    if (!(alpha_B > 0.0) || !(C > 0.0)) return ART_EINVAL;
+    float* partials = nullptr;
+    const int rc = static_partials(&partials);
+    if (rc != ART_OK) return rc;
+    // one tile of 256 cells per block: every partial read below is written first by its
+    // block in this call, so nothing carries over from an earlier call
+    const int tiles = (int)((ncell + 255) / 256);
+    cudaStream_t s = (cudaStream_t)stream;
+    k_dt_partial<<<tiles, 256, 0, s>>>(ncell, d_gamma, d_nH, d_xn, (float)alpha_B, partials);
+    k_dt_final<<<1, 1024, 0, s>>>(tiles, partials, C, d_dt);
     return cudaGetLastError() == cudaSuccess ? ART_OK : ART_ECUDA;
 }
 
