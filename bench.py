@@ -37,6 +37,8 @@ CONFIGS = {
                            alpha=2e-4, x0=1e-3),
     "c3_256_64src": dict(n=256, sigma_ln=2.0, nsrc=64, seed=3, nbar=1.0, sigma_H=10.0,
                          alpha=None, x0=1.0),
+    "c4_128_16src": dict(n=128, sigma_ln=1.5, nsrc=16, seed=4, nbar=1.0, sigma_H=10.0,
+                         alpha=None, x0=1.0),
     # small case of the same kernel for ncu captures (a few hundred MB on the device)
     "c3_256_8src": dict(n=256, sigma_ln=2.0, nsrc=8, seed=3, nbar=1.0, sigma_H=10.0,
                         alpha=None, x0=1.0),
@@ -126,43 +128,70 @@ def run_ours(args, rank, world, local_rank):
     xn = torch.full_like(nH, x0)
     nH0 = (xn * nH).contiguous()
     stream = torch.cuda.Stream(dev)
+    p = A.Params(level0=4, m_ray=4.0, tau_max=30.0, sigma_H=cfg["sigma_H"],
+                 schedule=args.schedule, chunk=args.chunk, block_threads=args.block_threads)
+    tuned = None
+    if args.tune and args.schedule == "persistent" and not args.chunk and not args.block_threads:
+        from paper_1711_06277_gb300 import autotune
+        with torch.cuda.stream(stream):
+            p = autotune.tune(nH0, 1.0 / n, pos, L, p)
+        tuned = {"chunk": p.chunk, "block_threads": p.block_threads,
+                 "queue_capacity": p.queue_capacity}
     with torch.cuda.stream(stream):
         grid = A.Grid(nH0, 1.0 / n, stream=stream)
         grid.add_sources(pos, L)
-    p = A.Params(level0=4, m_ray=4.0, tau_max=30.0, sigma_H=cfg["sigma_H"],
-                 schedule=args.schedule, chunk=args.chunk, block_threads=args.block_threads)
     gamma = torch.empty_like(nH)
     alpha = cfg["alpha"]
     dt = 0.1 / (alpha * cfg["nbar"]) if alpha else 0.0
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
 
-    def step(timed_trace=None):
+    def enqueue_step():
+        grid.trace(p, force=False, stats=False, out={"gamma": gamma})
+        if alpha:
+            A.xn_update(gamma, nH, xn, alpha, dt, nH0_out=nH0, stream=stream)
+
+    # warm-up (the first trace allocates ray buffers and direction tables)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            enqueue_step()
+            grid.stats()
+    graph = None
+    graph_note = None
+    if args.graph:
+        try:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=stream):
+                enqueue_step()
+            torch.cuda.synchronize(dev)
+        except Exception as e:  # report and run eagerly
+            graph, graph_note = None, f"capture failed: {type(e).__name__}: {e}"[:200]
+
+    def step():
         with torch.cuda.stream(stream):
-            if timed_trace is not None:
-                timed_trace[0].record(stream)
-            out = grid.trace(p, force=False, stats=True, out={"gamma": gamma})
-            if timed_trace is not None:
-                timed_trace[1].record(stream)
-            if alpha:
-                A.xn_update(gamma, nH, xn, alpha, dt, nH0_out=nH0, stream=stream)
-        return out["stats"]
+            if graph is not None:
+                graph.replay()
+            else:
+                enqueue_step()
 
-    for _ in range(args.warmup):
-        step()
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize(dev)
     cross = 0
-    trace_ms = []
-    tev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    step_ms = []
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    sev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     with ClockSampler(local_rank) as clk:
         ev[0].record(stream)
         for _ in range(args.steps):
-            st = step(tev)
+            sev[0].record(stream)
+            step()
+            sev[1].record(stream)
+            st = grid.stats()  # synchronizes; the counters of this step's trace
+            if st["status"] != 0:
+                raise RuntimeError(f"trace status {st['status']}")
             cross += st["crossings"]
-            trace_ms.append(tev[0].elapsed_time(tev[1]))
+            step_ms.append(sev[0].elapsed_time(sev[1]))
         ev[1].record(stream)
         torch.cuda.synchronize(dev)
     if world > 1:
@@ -179,16 +208,18 @@ def run_ours(args, rank, world, local_rank):
         ms_all, cross_all = ms, float(cross)
     value = cross_all / (ms_all / 1e3)
 
-    # dominant kernel: the persistent trace (its API call, incl. the small set-up kernels)
+    # dominant kernel: the persistent trace. Its launch time is taken from events around
+    # each step on the trace's stream; the other kernels of a step (opacity, injection,
+    # finalize, x_n update: ~5 GB of streaming traffic at 512^3) add well under 0.1 %.
     peak, peak_kind = _measured_peaks()
-    trace_s = statistics.mean(trace_ms) / 1e3
+    trace_s = statistics.mean(step_ms) / 1e3
     per_launch_cross = cross / args.steps
     achieved = per_launch_cross * BYTES_PER_CROSSING / trace_s / 1e9
 
     # end to end through the public API with host buffers (pinned): H2D of the neutral
     # density, trace + update, D2H of the updated neutral fraction
     e2e = None
-    if not args.no_e2e:
+    if args.e2e_steps > 0:
         h_in = torch.empty(nH0.shape, dtype=torch.float32, pin_memory=True)
         h_in.copy_(nH0.cpu())
         h_out = torch.empty_like(h_in, pin_memory=True)
@@ -196,35 +227,71 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e_steps = max(1, min(args.steps, 3))
         with torch.cuda.stream(stream):
             e0.record(stream)
-            for _ in range(e_steps):
+            for _ in range(args.e2e_steps):
                 nH0.copy_(h_in, non_blocking=True)
-                st = step()
+                enqueue_step()
                 h_out.copy_(xn, non_blocking=True)
-                e_cross += st["crossings"]
+                e_cross += grid.stats()["crossings"]
             e1.record(stream)
         torch.cuda.synchronize(dev)
         e_ms = e0.elapsed_time(e1)
         nbytes = nH0.numel() * 4
         e2e = {"value": e_cross / (e_ms / 1e3), "unit": "crossings/s",
-               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": e_steps}
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "steps": args.e2e_steps}
 
     extra = {}
-    if args.compare_plain and rank == 0:
+    if rank == 0 and args.compare_plain:
         extra["plain_vs_persistent"] = compare_schedules(A, dev)
+    if rank == 0 and args.adjoint:
+        extra["adjoint"] = adjoint_ratio(A, dev)
     grid.close()
+    launches = 5 if alpha else 4
     return {
         "value": value, "ms": ms_all, "cross": cross_all, "clocks": clk.summary(),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "k_trace_persistent (art_trace call)",
+                     "kernel": "k_trace_persistent",
                      "bytes_per_crossing": BYTES_PER_CROSSING,
                      "crossings_per_launch": per_launch_cross,
                      "launch_ms": trace_s * 1e3},
-        "e2e": e2e, "extra": extra,
+        "e2e": e2e, "extra": extra, "tuned": tuned,
+        "graph": graph is not None, "graph_note": graph_note,
+        "gpu_launches": launches * args.steps,
     }
+
+
+def adjoint_ratio(A, dev):
+    """Forward trace vs hand-written adjoint, 128^3 lognormal, 16 sources, loss = sum w gamma."""
+    import torch
+    cfg = CONFIGS["c4_128_16src"]
+    nH_h, pos, L = make_workload(cfg)
+    nH0 = torch.from_numpy(nH_h).to(dev)
+    w = torch.from_numpy(synth.uniform_weights(cfg["n"], seed=cfg["seed"]).astype(np.float32)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    g = A.Grid(nH0, 1.0 / cfg["n"], stream=stream)
+    g.add_sources(pos, L)
+    p = A.Params(level0=4, tau_max=30.0, sigma_H=cfg["sigma_H"])
+    g.trace(p, force=False)
+    g.trace_backward(p, w)
+    tf, tb = [], []
+    for _ in range(3):
+        for lst, fn in ((tf, lambda: g.trace(p, force=False, stats=False)),
+                        (tb, lambda: g.trace_backward(p, w, stats=False))):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            lst.append(e0.elapsed_time(e1))
+    st = g.stats()
+    g.close()
+    return {"workload": "128^3 lognormal sigma_ln=1.5, 16 sources, loss = sum w gamma",
+            "forward_ms": min(tf), "backward_ms": min(tb), "ratio": min(tb) / min(tf),
+            "crossings": st["crossings"]}
 
 
 def compare_schedules(A, dev):
@@ -289,14 +356,21 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c5_512_1024src", choices=sorted(CONFIGS))
     ap.add_argument("--schedule", default="persistent", choices=["persistent", "plain"])
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--block-threads", type=int, default=0)
-    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-e2e", dest="e2e_steps", action="store_const", const=0)
+    ap.add_argument("--graph", action="store_true", default=True)
+    ap.add_argument("--no-graph", dest="graph", action="store_false")
+    ap.add_argument("--tune", action="store_true", default=True)
+    ap.add_argument("--no-tune", dest="tune", action="store_false")
+    ap.add_argument("--adjoint", action="store_true", default=True)
+    ap.add_argument("--no-adjoint", dest="adjoint", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-plain", action="store_true", default=True)
     ap.add_argument("--no-compare-plain", dest="compare_plain", action="store_false")
@@ -310,6 +384,7 @@ def main():
                           f"power-law sources, l0=4, m_ray=4, tau_max=30"
                           + (", trace + Eq. e:xn3 update per step" if cfg["alpha"] else ""),
               "grid": cfg["n"], "sources": cfg["nsrc"], "schedule": args.schedule,
+              "cuda_graph": args.graph,
               "l2": "inputs larger than L2 (512 MB density, 2 GB accumulator)"}
 
     if args.impl == "reference":
@@ -342,12 +417,17 @@ def main():
         rr = run_reference(ra)
         cpu = {"value": rr["value"], "unit": "crossings/s", "cores": rr["threads"],
                "kind": "oracle", "sample": rr["sample"]}
+    config["cuda_graph"] = r["graph"]
+    if r["graph_note"]:
+        config["cuda_graph_note"] = r["graph_note"]
+    if r["tuned"]:
+        config["autotuned"] = r["tuned"]
     line = {"metric": "cell-segment crossings/s", "value": r["value"], "unit": "crossings/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
             "clocks": r["clocks"], "roofline": r["roofline"], "cpu_baseline": cpu,
-            "e2e": r["e2e"], "gpu_launches": 5 * args.steps}
+            "e2e": r["e2e"], "gpu_launches": r["gpu_launches"]}
     line.update(r["extra"])
     print(json.dumps(line), flush=True)
 

@@ -217,35 +217,33 @@ struct StepOut {
 };
 
 // (1 - e^-x)/x for x >= 0: Taylor series below 1 (no cancellation), exponential above.
+// Both branches are evaluated and one is selected, so lanes never diverge here.
 __device__ __forceinline__ float phi_of(float x)
 {
-    if (x < 1.f) {
-        float r = -1.f / 479001600.f;          // -1/12!
-        r = fmaf(r, x, 1.f / 39916800.f);
-        r = fmaf(r, x, -1.f / 3628800.f);
-        r = fmaf(r, x, 1.f / 362880.f);
-        r = fmaf(r, x, -1.f / 40320.f);
-        r = fmaf(r, x, 1.f / 5040.f);
-        r = fmaf(r, x, -1.f / 720.f);
-        r = fmaf(r, x, 1.f / 120.f);
-        r = fmaf(r, x, -1.f / 24.f);
-        r = fmaf(r, x, 1.f / 6.f);
-        r = fmaf(r, x, -0.5f);
-        return fmaf(r, x, 1.f);
-    }
-    return __fdividef(1.f - __expf(-x), x);
+    const float xs = fminf(x, 1.f);
+    float r = -1.f / 479001600.f;          // -1/12!
+    r = fmaf(r, xs, 1.f / 39916800.f);
+    r = fmaf(r, xs, -1.f / 3628800.f);
+    r = fmaf(r, xs, 1.f / 362880.f);
+    r = fmaf(r, xs, -1.f / 40320.f);
+    r = fmaf(r, xs, 1.f / 5040.f);
+    r = fmaf(r, xs, -1.f / 720.f);
+    r = fmaf(r, xs, 1.f / 120.f);
+    r = fmaf(r, xs, -1.f / 24.f);
+    r = fmaf(r, xs, 1.f / 6.f);
+    r = fmaf(r, xs, -0.5f);
+    r = fmaf(r, xs, 1.f);
+    const float xl = fmaxf(x, 1.f);
+    const float e = __fdividef(1.f - __expf(-xl), xl);
+    return x < 1.f ? r : e;
 }
 
-// Advances axis a (compile-time index) by one face.
-template <int a>
-__device__ __forceinline__ void walk_advance(Walk& W)
-{
-    W.rem[a] -= 1;
-    W.t[a] = df_add(W.t[a], W.d[a]);
-}
+__device__ __forceinline__ df df_sel(bool c, df a, df b) { return {c ? a.hi : b.hi, c ? a.lo : b.lo}; }
 
 // One step of the walk: the segment from tc to the next face or to the split radius rmax
-// (when the ray splits at all).
+// (when the ray splits at all). The common case (one axis crossing) runs without branches;
+// faces crossed together (ties) take a short side path. When the step ends the ray (event
+// other than EV_NONE) the walk state other than L and tau is left unspecified.
 template <bool kCountOnly>
 __device__ __forceinline__ StepOut walk_step(Walk& W, bool splits, df rmax, int sy, int sz,
                                              const float* __restrict__ chi_arr, float tau_max)
@@ -253,78 +251,62 @@ __device__ __forceinline__ StepOut walk_step(Walk& W, bool splits, df rmax, int 
     StepOut o;
     // earliest face crossing (lexicographic order of the normalised df values)
     const bool c01 = df_le(W.t[0], W.t[1]);
-    df tm = c01 ? W.t[0] : W.t[1];
+    df tm = df_sel(c01, W.t[0], W.t[1]);
     int a = c01 ? 0 : 1;
-    if (!df_le(tm, W.t[2])) {
-        tm = W.t[2];
-        a = 2;
-    }
+    const bool c2 = df_le(tm, W.t[2]);
+    tm = df_sel(c2, tm, W.t[2]);
+    a = c2 ? a : 2;
     const bool split = splits && df_le(rmax, tm);
-    const df tend = split ? rmax : tm;
-    o.ds = df_diff(tend, W.tc);
+    o.ds = df_diff(split ? rmax : tm, W.tc);
     // axes crossing together with the earliest one (relative tie 1e-12): a diagonal step
     const float tol = 1e-12f * tm.hi;
-    const int mask = (df_diff(W.t[0], tm) <= tol ? 1 : 0) | (df_diff(W.t[1], tm) <= tol ? 2 : 0) |
-                     (df_diff(W.t[2], tm) <= tol ? 4 : 0);
-    const bool single = mask == (1 << a);
+    const bool m0 = df_diff(W.t[0], tm) <= tol;
+    const bool m1 = df_diff(W.t[1], tm) <= tol;
+    const bool m2 = df_diff(W.t[2], tm) <= tol;
     // next cell and whether it leaves the grid
-    int nidx = W.idx;
-    bool out = false;
-    if (single) {
-        const int r = a == 0 ? W.rem[0] : (a == 1 ? W.rem[1] : W.rem[2]);
-        const float na = a == 0 ? W.n[0] : (a == 1 ? W.n[1] : W.n[2]);
-        const int st = a == 0 ? 1 : (a == 1 ? sy : sz);
-        out = r == 0;
-        nidx += na > 0.f ? st : -st;
-    } else {
-        if (mask & 1) { out = out || W.rem[0] == 0; nidx += W.n[0] > 0.f ? 1 : -1; }
-        if (mask & 2) { out = out || W.rem[1] == 0; nidx += W.n[1] > 0.f ? sy : -sy; }
-        if (mask & 4) { out = out || W.rem[2] == 0; nidx += W.n[2] > 0.f ? sz : -sz; }
-    }
-    float nchi = 0.f;
-    if (!split && !out) nchi = __ldg(chi_arr + nidx);  // prefetch for the next step
-    // deposit in the current cell
-    o.cell = -1;
-    o.ev = EV_NONE;
+    const int nidx = W.idx + (m0 ? (W.n[0] > 0.f ? 1 : -1) : 0) + (m1 ? (W.n[1] > 0.f ? sy : -sy) : 0) +
+                     (m2 ? (W.n[2] > 0.f ? sz : -sz) : 0);
+    const bool out = (m0 && W.rem[0] == 0) || (m1 && W.rem[1] == 0) || (m2 && W.rem[2] == 0);
+    const bool go = !split && !out;
+    const float nchi = go ? __ldg(chi_arr + nidx) : 0.f;  // prefetch for the next step
+    // deposit in the current cell (segments of length <= 0 deposit nothing)
+    const bool seg = o.ds > 0.f;
+    const float ds = seg ? o.ds : 0.f;
+    const float x = W.chi * ds;
+    o.cell = seg ? W.idx : -1;
     o.Lin = W.L;
-    o.G = 0.f;
-    o.dL = 0.f;
-    o.dtau = 0.f;
-    o.phi = 1.f;
-    if (o.ds > 0.f) {
-        o.cell = W.idx;
-        const float x = W.chi * o.ds;
-        o.dtau = x;
-        if (!kCountOnly) {
-            const float ph = phi_of(x);
-            o.phi = ph;
-            o.G = W.L * o.ds * ph;
-            o.dL = W.L * x * ph;
-            W.L = W.L - o.dL;
-        }
-        W.tau += x;
-        if (W.tau > tau_max) o.ev = EV_DROP;
+    o.dtau = x;
+    if (!kCountOnly) {
+        const float ph = phi_of(x);
+        o.phi = ph;
+        o.G = W.L * ds * ph;
+        o.dL = W.L * x * ph;
+        W.L = W.L - o.dL;
+    } else {
+        o.phi = 1.f;
+        o.G = 0.f;
+        o.dL = 0.f;
     }
-    if (o.ev == EV_NONE) {
-        if (split) {
-            o.ev = EV_SPLIT;
-        } else if (out) {
-            o.ev = EV_EXIT;
-        } else {
-            if (single) {
-                if (a == 0) walk_advance<0>(W);
-                else if (a == 1) walk_advance<1>(W);
-                else walk_advance<2>(W);
-            } else {
-                if (mask & 1) walk_advance<0>(W);
-                if (mask & 2) walk_advance<1>(W);
-                if (mask & 4) walk_advance<2>(W);
-            }
-            W.tc = tm;
-            W.idx = nidx;
-            W.chi = nchi;
-        }
+    W.tau += x;
+    const bool drop = seg && W.tau > tau_max;
+    o.ev = drop ? EV_DROP : (split ? EV_SPLIT : (out ? EV_EXIT : EV_NONE));
+    // advance: the earliest axis by select, further tied axes on the side path
+    const df dsel = df_sel(a == 0, W.d[0], df_sel(a == 1, W.d[1], W.d[2]));
+    const df tn = df_add(tm, dsel);
+    W.t[0] = df_sel(a == 0, tn, W.t[0]);
+    W.t[1] = df_sel(a == 1, tn, W.t[1]);
+    W.t[2] = df_sel(a == 2, tn, W.t[2]);
+    W.rem[0] -= m0 ? 1 : 0;
+    W.rem[1] -= m1 ? 1 : 0;
+    W.rem[2] -= m2 ? 1 : 0;
+    if ((int)m0 + (int)m1 + (int)m2 > 1) {
+        if (m0 && a != 0) W.t[0] = df_add(W.t[0], W.d[0]);
+        if (m1 && a != 1) W.t[1] = df_add(W.t[1], W.d[1]);
+        if (m2 && a != 2) W.t[2] = df_add(W.t[2], W.d[2]);
     }
+    W.tc = tm;
+    W.idx = nidx;
+    W.chi = nchi;
     return o;
 }
 

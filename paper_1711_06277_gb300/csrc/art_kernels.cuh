@@ -252,7 +252,7 @@ __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
 }
 
 // Plain schedule: all rays of level l currently in its buffer.
-__global__ void k_trace_level(const __grid_constant__ TraceArgs A, int l)
+__global__ void __launch_bounds__(512, 2) k_trace_level(const __grid_constant__ TraceArgs A, int l)
 {
     Tally T = {0.0, 0.0, 0ull, 0ull};
     // a front that overflowed (status set by the writer) is cut at the buffer capacity
@@ -275,7 +275,7 @@ __global__ void k_reset_counts(Sched* sc)
 }
 
 // Persistent schedule: all sources, all levels, one cooperative launch.
-__global__ void k_trace_persistent(const __grid_constant__ TraceArgs A)
+__global__ void __launch_bounds__(512, 2) k_trace_persistent(const __grid_constant__ TraceArgs A)
 {
     Tally T = {0.0, 0.0, 0ull, 0ull};
     Sched* sc = A.sched;

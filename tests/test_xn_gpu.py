@@ -22,7 +22,8 @@ def _fields(n, seed):
     rng = np.random.default_rng(seed)
     nH = (10.0 ** rng.uniform(-1, 3, n)).astype(np.float32)
     xn = rng.random(n).astype(np.float32)
-    xn[:5] = [0.0, 1.0, 1e-6, 0.5, 0.999]
+    special = [0.0, 1.0, 1e-6, 0.5, 0.999][:n]
+    xn[:len(special)] = special
     gam = (10.0 ** rng.uniform(-4, 2, n)).astype(np.float32)
     gam[::7] = 0.0
     return nH, xn, gam
