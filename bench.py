@@ -39,7 +39,9 @@ CONFIGS = {
                          alpha=None, x0=1.0),
     "c4_128_16src": dict(n=128, sigma_ln=1.5, nsrc=16, seed=4, nbar=1.0, sigma_H=10.0,
                          alpha=None, x0=1.0),
-    # small case of the same kernel for ncu captures (a few hundred MB on the device)
+    # small cases of the same kernel for ncu captures (a few GB on the device at most)
+    "c5_512_8src": dict(n=512, sigma_ln=2.0, nsrc=8, seed=5, nbar=100.0, sigma_H=0.1,
+                        alpha=2e-4, x0=1e-3),
     "c3_256_8src": dict(n=256, sigma_ln=2.0, nsrc=8, seed=3, nbar=1.0, sigma_H=10.0,
                         alpha=None, x0=1.0),
 }
@@ -197,15 +199,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     ms = ev[0].elapsed_time(ev[1])
-    tot = torch.tensor([ms, float(cross)], dtype=torch.float64, device=dev)
-    if world > 1:
-        mx = tot.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = tot.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms_all, cross_all = float(mx[0]), float(sm[1])
-    else:
-        ms_all, cross_all = ms, float(cross)
+    ms_all, cross_all = reduce_over_ranks(ms, cross, dev if world > 1 else None)
     value = cross_all / (ms_all / 1e3)
 
     # dominant kernel: the persistent trace. Its launch time is taken from events around
@@ -261,6 +255,22 @@ def run_ours(args, rank, world, local_rank):
         "graph": graph is not None, "graph_note": graph_note,
         "gpu_launches": launches * args.steps,
     }
+
+
+def reduce_over_ranks(ms: float, crossings: float, device=None):
+    """Whole-job timing of N replicas: the slowest rank's time and every rank's crossings.
+    Timing only -- no field data crosses ranks. Without an initialised process group it
+    returns its inputs."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(crossings)
+    t = torch.tensor([ms, float(crossings)], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    mx, sm = t.clone(), t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
 
 
 def adjoint_ratio(A, dev):

@@ -52,28 +52,6 @@ __device__ __forceinline__ float dphi_of(float x, float em)
     return ((1.f + x) * (1.f + em) - 1.f) / (x * x);
 }
 
-// Scalar version of the warp-merged deposit: runs of equal cells in lane order are summed
-// and written by their first lane.
-__device__ __forceinline__ void deposit_warp1(float* __restrict__ out, int cell, float v)
-{
-    const unsigned lane = threadIdx.x & 31u;
-    int prev = __shfl_up_sync(kFull, cell, 1);
-    bool dup = lane > 0 && cell >= 0 && prev == cell;
-    unsigned dups = __ballot_sync(kFull, dup);
-    if (dups) {
-        unsigned heads = ~dups;
-        unsigned after = lane == 31 ? 0u : heads & ~((2u << lane) - 1u);
-        int run_end = after ? __ffs(after) - 1 : 32;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            float o = __shfl_down_sync(kFull, v, off);
-            if ((int)lane + off < run_end) v += o;
-        }
-        if (dup) cell = -1;
-    }
-    if (cell >= 0) atomicAdd(out + cell, v);
-}
-
 struct DLacc {
     double v;
     unsigned src;
@@ -212,7 +190,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
                     }
                 }
             }
-            deposit_warp1(A.grad, cell, val);
+            if (cell >= 0) atomicAdd(A.grad + cell, val);
         }
         const unsigned sm = __ballot_sync(kFull, want_split);
         if (sm) {
@@ -240,7 +218,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
     T.crossings += ncross;
 }
 
-__global__ void k_backward_persistent(const __grid_constant__ TraceArgs A)
+__global__ void __launch_bounds__(256, 3) k_backward_persistent(const __grid_constant__ TraceArgs A)
 {
     Tally T = {0.0, 0.0, 0ull, 0ull};
     DLacc D = {0.0, 0xffffffffu};
@@ -368,7 +346,8 @@ extern "C" int art_trace_backward(art_grid* g, const art_params* p, const float*
     A.srcL = g->d_srcL;
     const double dV = g->dx * g->dx * g->dx;
     A.gscale = (float)(p->sigma_H * g->dx / dV);
-    const int threads = p->block_threads > 0 ? p->block_threads : 256;
+    // the reverse sweep is compiled for blocks of at most 256 threads (register budget)
+    const int threads = p->block_threads > 0 && p->block_threads < 256 ? p->block_threads : 256;
     int per_sm = 0;
     if ((rc = status_of(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_persistent,
                                                                       threads, 0))))

@@ -310,31 +310,10 @@ __device__ __forceinline__ StepOut walk_step(Walk& W, bool splits, df rmax, int 
     return o;
 }
 
-// Merges deposits of adjacent lanes that hit the same cell (runs of equal cell index in
-// lane order), then issues one 16-byte vector reduction per run head. Warp-uniform.
-__device__ __forceinline__ void deposit_warp(float4* __restrict__ acc, int cell, float4 v)
+// One 16-byte vector reduction (G, dL n) into the accumulator of `cell` (none if < 0).
+// Merging equal cells across lanes first was measured slower than letting L2 combine them.
+__device__ __forceinline__ void deposit(float4* __restrict__ acc, int cell, float4 v)
 {
-    const unsigned lane = threadIdx.x & 31u;
-    int prev = __shfl_up_sync(kFull, cell, 1);
-    bool dup = lane > 0 && cell >= 0 && prev == cell;
-    unsigned dups = __ballot_sync(kFull, dup);
-    if (dups) {
-        unsigned heads = ~dups;
-        unsigned after = heads & ~((2u << lane) - 1u);
-        if (lane == 31) after = 0;
-        int run_end = after ? __ffs(after) - 1 : 32;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            float ox = __shfl_down_sync(kFull, v.x, off);
-            float oy = __shfl_down_sync(kFull, v.y, off);
-            float oz = __shfl_down_sync(kFull, v.z, off);
-            float ow = __shfl_down_sync(kFull, v.w, off);
-            if ((int)lane + off < run_end) {
-                v.x += ox; v.y += oy; v.z += oz; v.w += ow;
-            }
-        }
-        if (dup) cell = -1;
-    }
     if (cell >= 0) {
         float* p = reinterpret_cast<float*>(acc + cell);
         asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x),

@@ -223,7 +223,7 @@ __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
                     }
                 }
             }
-            deposit_warp(A.acc, cell, dv);
+            deposit(A.acc, cell, dv);
         }
         // append the children of split rays to the next level
         const unsigned sm = __ballot_sync(kFull, want_split);

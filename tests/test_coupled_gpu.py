@@ -1,0 +1,143 @@
+"""Config-5 scale: the coupled trace + neutral-fraction loop (Strömgren check at 256^3, GPU
+vs oracle iteration at 32^3), oracle parity on source subsets of the 256^3 and 512^3
+workloads, and full-size properties of the 512^3 / 1024-source trace."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_1711_06277_gb300 import synth
+from tests import parity as PA
+
+pytestmark = pytest.mark.gpu
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")))
+
+
+@pytest.fixture(scope="module")
+def art():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1711_06277_gb300 import art as A
+    return A
+
+
+def _stromgren_setup(N):
+    g = GOLD["rtype_front"]
+    side, nH, alpha = g["box_over_R_St"], 1.0, 1.0
+    Q = 4 * math.pi / 3  # code units: R_St = 1, t_rec = 1
+    dx = side / N
+    sigma = g["dtau_cell_128"] * (128 / N) / (nH * dx)
+    pos = np.array([[(N // 2 + 0.5) * dx] * 3])
+    return dx, sigma, pos, Q, nH, alpha
+
+
+def _gpu_stromgren(A, N, steps, dt=0.5):
+    dx, sigma, pos, Q, nH, alpha = _stromgren_setup(N)
+    nHt = torch.full((N, N, N), nH, device="cuda")
+    xn = torch.ones_like(nHt)
+    nH0 = xn * nHt
+    g = A.Grid(nH0, dx)
+    g.add_sources(pos, [Q])
+    p = A.Params(level0=4, tau_max=30.0, sigma_H=sigma)
+    gam = torch.empty_like(nHt)
+    for _ in range(steps):
+        out = g.trace(p, force=False, out={"gamma": gam})
+        assert out["stats"]["status"] == 0
+        A.xn_update(gam, nHt, xn, alpha, dt, nH0_out=nH0)
+    x = xn.double().cpu().numpy()
+    g.close()
+    R = (3 * (x < 0.5).sum() * dx**3 / (4 * math.pi)) ** (1 / 3)
+    rec = (alpha * (nH * (1 - x)) ** 2).sum() * dx**3
+    return x, R, rec / Q
+
+
+def test_stromgren_256(art):
+    _, R, bal = _gpu_stromgren(art, 256, 240)
+    assert R == pytest.approx(1.0, rel=0.01)      # paper: < 1 % at 8 t_rec
+    assert bal == pytest.approx(1.0, rel=1e-3)
+
+
+def test_coupled_loop_matches_oracle_32(art):
+    N, steps = 32, 60
+    x_gpu, R_gpu, bal_gpu = _gpu_stromgren(art, N, steps)
+    dx, sigma, pos, Q, nH, alpha = _stromgren_setup(N)
+    xn = np.ones((N, N, N))
+    for _ in range(steps):
+        prob = O.Problem(nH0=(xn * nH).astype(np.float32), pos=pos, L=[Q], dx=dx,
+                         sigma_H=sigma, level0=4, tau_max=30.0)
+        xn = O.xn_method_b(xn, O.trace(prob, nthreads=8).gamma, nH, alpha, 0.5)
+    assert np.abs(x_gpu - xn).max() < 1e-3
+    assert bal_gpu == pytest.approx(float((alpha * (nH * (1 - xn)) ** 2).sum() * dx**3 / Q), rel=1e-4)
+
+
+def _workload(n, sigma_ln, nsrc, seed):
+    rho = synth.lognormal_field(n, sigma_ln, seed=seed).astype(np.float32)
+    return rho, synth.uniform_positions(nsrc, seed=seed), synth.power_law_luminosities(nsrc, seed=seed)
+
+
+def _subset_parity(A, nH0, pos, L, dx, sigma_H):
+    dev = torch.device("cuda")
+    p = A.Params(level0=4, tau_max=30.0, sigma_H=sigma_H)
+    g = A.Grid(torch.from_numpy(nH0).to(dev), dx)
+    g.add_sources(pos, L)
+    out = g.trace(p, force=True, energy=True)
+    res = {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in out.items()}
+    g.close()
+    ref = O.trace(O.Problem(nH0=nH0, pos=pos, L=L, dx=dx, sigma_H=sigma_H, level0=4,
+                            tau_max=30.0), nthreads=os.cpu_count() or 8)
+    st = res["stats"]
+    PA.compare_field(res["gamma"], ref.gamma, what="gamma")
+    chi = nH0.astype(np.float64) * sigma_H
+    PA.compare_force(res["force"], ref.force, chi * ref.energy)
+    assert abs(st["crossings"] - ref.crossings) <= max(0, ref.near_tie_rays) * 4
+    assert abs(st["L_escaped"] - ref.escaped) <= PA.CONS * ref.L_in
+    assert st["destroy"] == st["destroy_expected"]
+
+
+def test_config3_source_subset_parity(art):
+    n = 256
+    rho, pos, L = _workload(n, 2.0, 64, seed=3)
+    _subset_parity(art, rho, pos[:4], L[:4], 1.0 / n, 10.0)
+
+
+def test_config5_source_subset_parity(art):
+    n = 512
+    rho, pos, L = _workload(n, 2.0, 1024, seed=5)
+    nH = (100.0 * rho).astype(np.float32)
+    # fully neutral (tau_box = 10) for two sources, and the initial x_n = 1e-3 for one
+    _subset_parity(art, nH, pos[:2], L[:2], 1.0 / n, 0.1)
+    _subset_parity(art, (1e-3 * nH).astype(np.float32), pos[2:3], L[2:3], 1.0 / n, 0.1)
+
+
+def test_config5_full_size_properties(art):
+    """All 1024 sources in the launch configuration the bench times: photon conservation,
+    the destroy counter, and additivity over two halves of the sources (which with the
+    subset parity above ties the full trace to the oracle). Each cell sums ~10^4 FP32
+    deposits here, so additivity is checked at 5e-5 (the FP32 summation bound)."""
+    n = 512
+    rho, pos, L = _workload(n, 2.0, 1024, seed=5)
+    nH0 = torch.from_numpy((1e-3 * 100.0 * rho).astype(np.float32)).cuda()
+    p = art.Params(level0=4, tau_max=30.0, sigma_H=0.1)
+    g = art.Grid(nH0, 1.0 / n)
+    g.add_sources(pos, L)
+    full = g.trace(p, force=False, energy=True)
+    st = full["stats"]
+    assert st["status"] == 0 and st["destroy"] == st["destroy_expected"]
+    G = full["energy"].double() * (1.0 / n) ** 3
+    chi = nH0.double() * 0.1
+    absorbed = float((chi * G).sum())
+    assert abs(absorbed + st["L_escaped"] + st["L_dropped"] - st["L_in"]) <= PA.CONS * st["L_in"]
+    gam_full = full["gamma"].double().cpu().numpy()
+    del full, G, chi
+    halves = []
+    for sl in (slice(0, 512), slice(512, 1024)):
+        g.clear_sources()
+        g.add_sources(pos[sl], L[sl])
+        halves.append(g.trace(p, force=False)["gamma"].double().cpu().numpy())
+    g.close()
+    PA.compare_field(gam_full, halves[0] + halves[1], rel=5e-5, what="additivity")

@@ -121,3 +121,26 @@ def test_stromgren_radius_numbers():
     assert g["box_pc"] / (R / pc) == pytest.approx(g["box_over_R_St"], rel=0.01)
     dtau = g["n_H"] * g["sigma_H"] * g["box_pc"] * pc / 128
     assert dtau == pytest.approx(g["dtau_cell_128"], rel=0.01)
+
+
+def test_stromgren_sphere_equilibrium():
+    """Trace + Eq. e:xn3 iterated to equilibrium around one source in a uniform medium
+    (Sec. 3.3.1 set-up in code units: R_St = 1, t_rec = 1, box 2.4 R_St, dtau per neutral cell
+    109 (128/N)): the ionized volume matches (3Q/(4 pi alpha n^2))^(1/3) and recombinations
+    balance the source (the dust-free photon budget of Eq. e:xn at equilibrium)."""
+    g = GOLD["rtype_front"]
+    N, side, nH, alpha = 32, g["box_over_R_St"], 1.0, 1.0
+    Q = 4 * math.pi / 3  # R_St = 1
+    dx = side / N
+    sigma = g["dtau_cell_128"] * (128 / N) / (nH * dx)
+    pos = np.array([[(N // 2 + 0.5) * dx] * 3])
+    xn = np.ones((N, N, N))
+    for _ in range(80):
+        prob = O.Problem(nH0=(xn * nH).astype(np.float32), pos=pos, L=[Q], dx=dx,
+                         sigma_H=sigma, level0=4, tau_max=30.0)
+        r = O.trace(prob, nthreads=4)
+        xn = O.xn_method_b(xn, r.gamma, nH, alpha, 0.5)
+    R = (3 * (xn < 0.5).sum() * dx**3 / (4 * math.pi)) ** (1 / 3)
+    rec = (alpha * (nH * (1 - xn)) ** 2).sum() * dx**3
+    assert R == pytest.approx(1.0, rel=0.02)
+    assert rec / Q == pytest.approx(1.0, rel=1e-3)
