@@ -86,6 +86,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
     unsigned long long* child_count = &A.sched->count[l + 1];
     const float gs = A.gscale;
     const int sy = A.nx, sz = A.nx * A.ny;
+    const MemPolicy mp = make_policy(A.l2_hints);
     const double nan = __longlong_as_double(0x7ff8000000000000ll);
 
     unsigned long long wnext = 0, wend = 0;
@@ -152,7 +153,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
             if (mode != 0) {
                 const float wv = __ldg(A.w + W.idx);
                 const float hv = mode == 2 ? __ldg(A.chiH + W.idx) : 0.f;
-                const StepOut o = walk_step<false>(W, splits, LV.rmax, sy, sz, A.chi, A.tau_max);
+                const StepOut o = walk_step<false>(W, splits, LV.rmax, sy, sz, A.chi, A.tau_max, mp);
                 if (o.cell >= 0) {
                     const float g = wv * gs * o.G;
                     if (mode == 1) {

@@ -91,6 +91,7 @@ int check_params(const art_params* p)
         return ART_EINVAL;
     if (p->chunk != 0 && (p->chunk < 32 || p->chunk % 32 != 0)) return ART_EINVAL;
     if (p->queue_capacity != 0 && p->queue_capacity < 4) return ART_EINVAL;
+    if (p->l2_hints < 0 || p->l2_hints > 3 || p->blocks_per_sm < 0) return ART_EINVAL;
     if (p->flags & ART_F_ROTATE)
         for (int i = 0; i < 9; ++i)
             if (!std::isfinite(p->rot[i])) return ART_EINVAL;
@@ -268,6 +269,7 @@ TraceArgs make_args(art_grid* g, const art_params* p)
     A.stats = g->d_stats;
     double ws = p->wait_limit_s == 0.0 ? kDefaultWaitS : p->wait_limit_s;
     A.wait_ns = ws < 0.0 ? -1 : (long long)(ws * 1e9);
+    A.l2_hints = p->l2_hints;
     return A;
 }
 
@@ -428,6 +430,7 @@ int art_trace(art_grid* g, const art_params* p, float* d_gamma, float* d_force, 
         int per_sm = 0;
         ART_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent, threads, 0));
         if (per_sm < 1) return ART_EINVAL;
+        if (p->blocks_per_sm > 0 && p->blocks_per_sm < per_sm) per_sm = p->blocks_per_sm;
         cudaLaunchConfig_t cfg;
         std::memset(&cfg, 0, sizeof(cfg));
         cfg.gridDim = dim3(per_sm * g->sms);

@@ -149,11 +149,57 @@ struct TraceArgs {
     Sched* sched;
     DevStats* stats;
     long long wait_ns;       // bound of a grid-barrier wait (<0: give up at once)
+    int l2_hints;            // see art_params.l2_hints
     float gscale;            // adjoint: sigma_H * dx / dV (gamma per unit G)
     const float* srcL;       // adjoint: source luminosities (gradients scale with them)
 };
 
 enum : int { EV_NONE = 0, EV_EXIT = 1, EV_DROP = 2, EV_SPLIT = 3 };
+
+// ---------------------------------------------------------------------------------------
+// memory access with an optional L2 eviction priority
+// ---------------------------------------------------------------------------------------
+struct MemPolicy {
+    unsigned long long gather, deposit;  // createpolicy values
+    bool hint_gather, hint_deposit;
+};
+
+__device__ __forceinline__ MemPolicy make_policy(int mode)
+{
+    MemPolicy m;
+    unsigned long long last, first;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(last));
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(first));
+    m.gather = last;
+    m.deposit = mode == 3 ? first : last;
+    m.hint_gather = mode >= 1;
+    m.hint_deposit = mode >= 2;
+    return m;
+}
+
+__device__ __forceinline__ float load_gather(const float* p, const MemPolicy& m)
+{
+    if (m.hint_gather) {
+        float v;
+        asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(m.gather));
+        return v;
+    }
+    return __ldg(p);
+}
+
+__device__ __forceinline__ void red_v4(float4* q, float4 v, const MemPolicy& m)
+{
+    float* p = reinterpret_cast<float*>(q);
+    if (m.hint_deposit) {
+        asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p),
+                     "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(m.deposit)
+                     : "memory");
+    } else {
+        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x),
+                     "f"(v.y), "f"(v.z), "f"(v.w)
+                     : "memory");
+    }
+}
 
 // ---------------------------------------------------------------------------------------
 // ray walk
@@ -246,7 +292,8 @@ __device__ __forceinline__ df df_sel(bool c, df a, df b) { return {c ? a.hi : b.
 // other than EV_NONE) the walk state other than L and tau is left unspecified.
 template <bool kCountOnly>
 __device__ __forceinline__ StepOut walk_step(Walk& W, bool splits, df rmax, int sy, int sz,
-                                             const float* __restrict__ chi_arr, float tau_max)
+                                             const float* __restrict__ chi_arr, float tau_max,
+                                             const MemPolicy& mp)
 {
     StepOut o;
     // earliest face crossing (lexicographic order of the normalised df values)
@@ -268,7 +315,7 @@ __device__ __forceinline__ StepOut walk_step(Walk& W, bool splits, df rmax, int 
                      (m2 ? (W.n[2] > 0.f ? sz : -sz) : 0);
     const bool out = (m0 && W.rem[0] == 0) || (m1 && W.rem[1] == 0) || (m2 && W.rem[2] == 0);
     const bool go = !split && !out;
-    const float nchi = go ? __ldg(chi_arr + nidx) : 0.f;  // prefetch for the next step
+    const float nchi = go ? load_gather(chi_arr + nidx, mp) : 0.f;  // prefetch for the next step
     // deposit in the current cell (segments of length <= 0 deposit nothing)
     const bool seg = o.ds > 0.f;
     const float ds = seg ? o.ds : 0.f;
@@ -310,16 +357,38 @@ __device__ __forceinline__ StepOut walk_step(Walk& W, bool splits, df rmax, int 
     return o;
 }
 
+// Merges the deposits of lanes that hit the same cell (runs of equal cell index in lane
+// order) and issues one reduction per run. Used only for the first segment of base-level
+// rays, which all start in their source's cell: at l0 = 8 that is 786,432 deposits into one
+// cell per source, whose FP32 sum the merge keeps accurate. Warp-uniform.
+__device__ __forceinline__ void deposit_merged(float4* __restrict__ acc, int cell, float4 v,
+                                               const MemPolicy& mp)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const int prev = __shfl_up_sync(kFull, cell, 1);
+    const bool dup = lane > 0 && cell >= 0 && prev == cell;
+    const unsigned dups = __ballot_sync(kFull, dup);
+    const unsigned after = lane == 31 ? 0u : ~dups & ~((2u << lane) - 1u);
+    const int run_end = after ? __ffs(after) - 1 : 32;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const float ox = __shfl_down_sync(kFull, v.x, off);
+        const float oy = __shfl_down_sync(kFull, v.y, off);
+        const float oz = __shfl_down_sync(kFull, v.z, off);
+        const float ow = __shfl_down_sync(kFull, v.w, off);
+        if ((int)lane + off < run_end) {
+            v.x += ox; v.y += oy; v.z += oz; v.w += ow;
+        }
+    }
+    if (cell >= 0 && !dup) red_v4(acc + cell, v, mp);
+}
+
 // One 16-byte vector reduction (G, dL n) into the accumulator of `cell` (none if < 0).
 // Merging equal cells across lanes first was measured slower than letting L2 combine them.
-__device__ __forceinline__ void deposit(float4* __restrict__ acc, int cell, float4 v)
+__device__ __forceinline__ void deposit(float4* __restrict__ acc, int cell, float4 v,
+                                        const MemPolicy& mp)
 {
-    if (cell >= 0) {
-        float* p = reinterpret_cast<float*>(acc + cell);
-        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x),
-                     "f"(v.y), "f"(v.z), "f"(v.w)
-                     : "memory");
-    }
+    if (cell >= 0) red_v4(acc + cell, v, mp);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -158,6 +158,7 @@ __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
     const RayBuf C = A.buf[l + 1];
     unsigned long long* child_count = &A.sched->count[l + 1];
     const int sy = A.nx, sz = A.nx * A.ny;
+    const MemPolicy mp = make_policy(A.l2_hints);
 
     unsigned long long wnext = 0, wend = 0;
     bool more = true;
@@ -166,6 +167,8 @@ __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
     unsigned s = 0, p = 0;
     float L0 = 0.f;
     bool splits = false;
+    bool first = false;  // next step is the first segment of a base-level ray
+    const bool base = l == A.level0;
     unsigned ncross = 0;
 
     for (;;) {
@@ -186,6 +189,7 @@ __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
                 if (!active && rank < avail) {
                     if (ray_begin(A, LV, B, l, wnext + rank, W, s, p, L0, splits)) {
                         active = true;
+                        first = base;
                     } else {  // starts outside the grid: escapes with its full luminosity
                         T.escaped += (double)L0;
                         T.destroy += LV.destroy_w;
@@ -206,7 +210,7 @@ __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
             int cell = -1;
             float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
             if (active) {
-                const StepOut o = walk_step<false>(W, splits, LV.rmax, sy, sz, A.chi, A.tau_max);
+                const StepOut o = walk_step<false>(W, splits, LV.rmax, sy, sz, A.chi, A.tau_max, mp);
                 if (o.cell >= 0) {
                     cell = o.cell;
                     dv = make_float4(o.G, o.dL * W.n[0], o.dL * W.n[1], o.dL * W.n[2]);
@@ -223,7 +227,9 @@ __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
                     }
                 }
             }
-            deposit(A.acc, cell, dv);
+            if (base && __any_sync(kFull, first)) deposit_merged(A.acc, cell, dv, mp);
+            else deposit(A.acc, cell, dv, mp);
+            first = false;
         }
         // append the children of split rays to the next level
         const unsigned sm = __ballot_sync(kFull, want_split);
