@@ -72,9 +72,6 @@ typedef struct {
     long long queue_capacity; /* rays per level buffer beyond l0 (0 = library choice) */
     double wait_limit_s; /* bound on any device-side wait (grid barrier); 0 = library default
                             (10 s); a negative value makes every wait give up at once */
-    int l2_hints;        /* L2 eviction priority of the trace's memory traffic: 0 none,
-                            1 opacity gathers evict-last, 2 gathers and deposits evict-last,
-                            3 gathers evict-last and deposits evict-first */
     int blocks_per_sm;   /* resident blocks per SM of the persistent trace (0 = as many as
                             fit); fewer blocks keep fewer rays in flight */
 } art_params;

@@ -48,7 +48,6 @@ class ArtParams(ctypes.Structure):
         ("chunk", ctypes.c_int),
         ("queue_capacity", ctypes.c_longlong),
         ("wait_limit_s", ctypes.c_double),
-        ("l2_hints", ctypes.c_int),
         ("blocks_per_sm", ctypes.c_int),
     ]
 

@@ -32,7 +32,6 @@ class Params:
     chunk: int = 0
     queue_capacity: int = 0
     wait_limit_s: float = 0.0
-    l2_hints: int = 0
     blocks_per_sm: int = 0
 
     def to_c(self) -> C.ArtParams:
@@ -54,7 +53,6 @@ class Params:
         p.chunk = int(self.chunk)
         p.queue_capacity = int(self.queue_capacity)
         p.wait_limit_s = float(self.wait_limit_s)
-        p.l2_hints = int(self.l2_hints)
         p.blocks_per_sm = int(self.blocks_per_sm)
         return p
 

@@ -21,6 +21,7 @@
 // The phase order is deepest-first, as in the forward schedule, so children always finish
 // before their parents' collapse and every level buffer stays bounded.
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 
 #include "art.h"
@@ -75,7 +76,7 @@ __device__ __forceinline__ df df_of(double v)
 
 // One phase of the reverse sweep on rays [cursor .. end) of level l. Warp-uniform.
 __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long long* cursor,
-                            unsigned long long end, Tally& T, DLacc& D)
+                            unsigned long long begin, unsigned long long end, Tally& T, DLacc& D)
 {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt = (1u << lane) - 1u;
@@ -83,24 +84,25 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
     const RayBuf B = A.buf[l];
     const RayBuf C = A.buf[l + 1];
     const RayBuf P = l > A.level0 ? A.buf[l - 1] : A.buf[l];
-    unsigned long long* child_count = &A.sched->count[l + 1];
+    const bool has_next = l < A.lmax_glob;
     const float gs = A.gscale;
     const int sy = A.nx, sz = A.nx * A.ny;
-    const MemPolicy mp = make_policy(A.l2_hints);
     const double nan = __longlong_as_double(0x7ff8000000000000ll);
 
-    unsigned long long wnext = 0, wend = 0;
+    // slot indices fit in 32 bits (level buffers hold fewer than 2^31 slots)
+    const unsigned b32 = (unsigned)begin, e32 = (unsigned)end;
+    unsigned wnext = 0, wend = 0;
     bool more = true;
     int mode = 0;  // 0 idle, 1 pass 1, 2 pass 2
-    Walk W;
+    WalkT<float4> W;
     unsigned s = 0, p = 0;
-    unsigned long long slot = 0;
+    unsigned slot = 0;
     float L0 = 0.f, Ls = 0.f;
     df own = {0.f, 0.f};   // own weighted sum (pass 1), kept for dL in pass 2
     double total = 0.0;    // own + descendants (pass 2)
     df rem = {0.f, 0.f};   // weighted sum over what follows the current segment (pass 2)
     bool splits = false;
-    unsigned ncross = 0;
+    unsigned ncross = 0, nrays = 0;
 
     for (;;) {
         unsigned need = __ballot_sync(kFull, mode == 0);
@@ -110,23 +112,28 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
                 if (lane == 0) b = atomicAdd(cursor, (unsigned long long)A.chunk);
                 b = __shfl_sync(kFull, b, 0);
                 if (b >= end) { more = false; break; }
-                wnext = b;
-                wend = min(b + (unsigned long long)A.chunk, end);
+                wnext = (unsigned)b;
+                wend = min(wnext + (unsigned)A.chunk, e32);
             }
-            const unsigned avail = (unsigned)min(wend - wnext, 32ull);
+            const unsigned avail = min(wend - wnext, 32u);
             const unsigned rank = __popc(need & lt);
             if (mode == 0 && rank < avail) {
                 slot = wnext + rank;
                 if (kind == PH_EXPAND) {
-                    const bool inside = ray_begin(A, LV, B, l, slot, W, s, p, L0, splits);
-                    Ls = __ldg(A.srcL + s);
-                    if (inside) {
+                    const int st = ray_begin(A, LV, B, l, slot, W, A.rec, s, p, L0, splits);
+                    if (st > 0) {
+                        Ls = __ldg(A.srcL + s);
                         mode = 1;
                         own = {0.f, 0.f};
-                    } else {  // no segment at all: a finished leaf with zero sums
-                        T.escaped += (double)L0;
-                        T.destroy += LV.destroy_w;
+                        ++nrays;
+                    } else {  // no ray, or no segment at all: a finished leaf with zero sums
+                        if (st == 0) {
+                            T.escaped += (double)L0;
+                            T.destroy += LV.destroy_w;
+                            ++nrays;
+                        }
                         B.own[slot] = nan;
+                        if (has_next) write_holes(C, 4ull * (slot - b32));
                     }
                 } else {
                     const double ov = __ldcg(B.own + slot);
@@ -134,7 +141,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
                         total = ov + __ldcg(B.sub + slot);
                         own = df_of(ov);
                         rem = df_of(total);
-                        ray_begin(A, LV, B, l, slot, W, s, p, L0, splits);
+                        ray_begin(A, LV, B, l, slot, W, A.rec, s, p, L0, splits);
                         Ls = __ldg(A.srcL + s);
                         mode = 2;
                     }
@@ -145,15 +152,14 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
         }
         if (!__any_sync(kFull, mode != 0)) break;
 
-        bool want_split = false;
 #pragma unroll 1
         for (int k = 0; k < 4; ++k) {
             int cell = -1;
             float val = 0.f;
             if (mode != 0) {
-                const float wv = __ldg(A.w + W.idx);
-                const float hv = mode == 2 ? __ldg(A.chiH + W.idx) : 0.f;
-                const StepOut o = walk_step<false>(W, splits, LV.rmax, sy, sz, A.chi, A.tau_max, mp);
+                const float wv = W.cell.z;   // weight and neutral-H opacity of this cell
+                const float hv = W.cell.y;
+                const StepOut o = walk_step<false>(W, splits, LV.rmax, sy, sz, A.rec, A.tau_max);
                 if (o.cell >= 0) {
                     const float g = wv * gs * o.G;
                     if (mode == 1) {
@@ -169,19 +175,33 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
                 }
                 if (o.ev != EV_NONE) {
                     if (mode == 1) {
+                        const unsigned long long c4 = 4ull * (slot - b32);
                         if (o.ev == EV_SPLIT) {
-                            want_split = true;
                             B.own[slot] = (double)own.hi + (double)own.lo;
                             B.sub[slot] = 0.0;
+                            if (c4 + 4 <= C.cap) {
+                                const float Lc = 0.25f * W.L;
+                                const unsigned ps = (unsigned)slot;
+                                *reinterpret_cast<uint4*>(C.src + c4) = make_uint4(s, s, s, s);
+                                *reinterpret_cast<uint4*>(C.pix + c4) =
+                                    make_uint4(4 * p, 4 * p + 1, 4 * p + 2, 4 * p + 3);
+                                *reinterpret_cast<float4*>(C.L + c4) = make_float4(Lc, Lc, Lc, Lc);
+                                *reinterpret_cast<float4*>(C.tau + c4) =
+                                    make_float4(W.tau, W.tau, W.tau, W.tau);
+                                *reinterpret_cast<uint4*>(C.parent + c4) = make_uint4(ps, ps, ps, ps);
+                            } else {
+                                atomicCAS(&A.stats->error, 0, -3);
+                            }
                             mode = 0;
                         } else {
                             if (o.ev == EV_EXIT) T.escaped += (double)W.L;
                             else T.dropped += (double)W.L;
                             T.destroy += LV.destroy_w;
+                            if (has_next) write_holes(C, c4);
                             B.own[slot] = nan;  // finished within this phase
                             total = (double)own.hi + (double)own.lo;
                             rem = own;
-                            ray_begin(A, LV, B, l, slot, W, s, p, L0, splits);
+                            ray_begin(A, LV, B, l, slot, W, A.rec, s, p, L0, splits);
                             mode = 2;
                         }
                     } else {
@@ -193,30 +213,9 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
             }
             if (cell >= 0) atomicAdd(A.grad + cell, val);
         }
-        const unsigned sm = __ballot_sync(kFull, want_split);
-        if (sm) {
-            unsigned long long base = 0;
-            const int leader = __ffs(sm) - 1;
-            if ((int)lane == leader) base = atomicAdd(child_count, 4ull * __popc(sm));
-            base = __shfl_sync(kFull, base, leader);
-            if (want_split) {
-                unsigned long long cs = base + 4ull * __popc(sm & lt);
-                if (cs + 4 <= C.cap) {
-                    const float Lc = 0.25f * W.L;
-                    const unsigned ps = (unsigned)slot;
-                    *reinterpret_cast<uint4*>(C.src + cs) = make_uint4(s, s, s, s);
-                    *reinterpret_cast<uint4*>(C.pix + cs) =
-                        make_uint4(4 * p, 4 * p + 1, 4 * p + 2, 4 * p + 3);
-                    *reinterpret_cast<float4*>(C.L + cs) = make_float4(Lc, Lc, Lc, Lc);
-                    *reinterpret_cast<float4*>(C.tau + cs) = make_float4(W.tau, W.tau, W.tau, W.tau);
-                    *reinterpret_cast<uint4*>(C.parent + cs) = make_uint4(ps, ps, ps, ps);
-                } else {
-                    atomicCAS(&A.stats->error, 0, -3);
-                }
-            }
-        }
     }
     T.crossings += ncross;
+    count_rays(A.stats, l, nrays);
 }
 
 __global__ void __launch_bounds__(256, 3) k_backward_persistent(const __grid_constant__ TraceArgs A)
@@ -225,7 +224,7 @@ __global__ void __launch_bounds__(256, 3) k_backward_persistent(const __grid_con
     DLacc D = {0.0, 0xffffffffu};
     Sched* sc = A.sched;
     __shared__ int s_level, s_kind;
-    __shared__ unsigned long long s_end;
+    __shared__ unsigned long long s_begin, s_end;
     for (;;) {
         if (!grid_barrier(sc, A.stats, A.wait_ns)) break;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -239,6 +238,7 @@ __global__ void __launch_bounds__(256, 3) k_backward_persistent(const __grid_con
                 v->chunk_state[l] = 0;
                 v->phase_level = l;
                 v->phase_kind = PH_COLLAPSE;
+                v->phase_begin = v->chunk_begin[l];
                 v->phase_end = v->chunk_end[l];
                 v->cursor[l] = v->chunk_begin[l];
             } else {
@@ -249,16 +249,15 @@ __global__ void __launch_bounds__(256, 3) k_backward_persistent(const __grid_con
                 v->count[l] = b;
                 v->phase_level = l;
                 v->phase_kind = PH_EXPAND;
+                v->phase_begin = b;
                 v->phase_end = have;
                 v->cursor[l] = b;
                 if (l < A.lmax_glob) {
                     v->chunk_state[l] = 1;
                     v->chunk_begin[l] = b;
                     v->chunk_end[l] = have;
+                    v->count[l + 1] = 4 * take;  // the children's slots
                 }
-                A.stats->rays_per_level[l] += take;
-                A.stats->rays_total += take;
-                if (l > A.stats->level_reached) A.stats->level_reached = l;
             }
             __threadfence();
         }
@@ -267,15 +266,26 @@ __global__ void __launch_bounds__(256, 3) k_backward_persistent(const __grid_con
             volatile Sched* v = sc;
             s_level = v->done ? -1 : v->phase_level;
             s_kind = v->phase_kind;
+            s_begin = v->phase_begin;
             s_end = v->phase_end;
         }
         __syncthreads();
         const int l = s_level;
         if (l < 0) break;
-        run_adjoint(A, l, s_kind, &sc->cursor[l], s_end, T, D);
+        run_adjoint(A, l, s_kind, &sc->cursor[l], s_begin, s_end, T, D);
     }
     if (D.src != 0xffffffffu && D.v != 0.0) atomicAdd(A.dL + D.src, D.v);
     tally_flush(T, A.stats);
+}
+
+// Per-cell record of the reverse sweep: one 16-byte gather per crossing.
+__global__ void k_pack_cells(long long ncell, const float* __restrict__ chi,
+                             const float* __restrict__ chiH, const float* __restrict__ w,
+                             float4* __restrict__ rec)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long step = (long long)gridDim.x * blockDim.x;
+    for (; i < ncell; i += step) rec[i] = make_float4(chi[i], chiH[i], w[i], 0.f);
 }
 
 __global__ void k_inject_all(int nsrc, unsigned npix0, RayBuf B, unsigned long long* count)
@@ -340,7 +350,15 @@ extern "C" int art_trace_backward(art_grid* g, const art_params* p, const float*
     k_inject_all<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(ns, npix0, g->buf[l0],
                                                             &g->d_sched->count[l0]);
     if ((rc = status_of(cudaGetLastError()))) return rc;
+    if (!g->d_rec && (rc = status_of(cudaMalloc((void**)&g->d_rec, sizeof(float4) * g->ncell))))
+        return rc;
+    {
+        const int blocks = (int)std::min<long long>((g->ncell + 255) / 256, (long long)g->sms * 16);
+        k_pack_cells<<<blocks, 256, 0, st>>>(g->ncell, g->d_chi, g->d_chiH, d_w, g->d_rec);
+        if ((rc = status_of(cudaGetLastError()))) return rc;
+    }
     TraceArgs A = make_args(g, p);
+    A.rec = g->d_rec;
     A.w = d_w;
     A.grad = d_dlog_nH0;
     A.dL = dL;

@@ -90,8 +90,9 @@ int check_params(const art_params* p)
         (p->block_threads % 32 != 0 || p->block_threads < 64 || p->block_threads > 1024))
         return ART_EINVAL;
     if (p->chunk != 0 && (p->chunk < 32 || p->chunk % 32 != 0)) return ART_EINVAL;
-    if (p->queue_capacity != 0 && p->queue_capacity < 4) return ART_EINVAL;
-    if (p->l2_hints < 0 || p->l2_hints > 3 || p->blocks_per_sm < 0) return ART_EINVAL;
+    if (p->queue_capacity != 0 && (p->queue_capacity < 4 || p->queue_capacity > (1ll << 30)))
+        return ART_EINVAL;
+    if (p->blocks_per_sm < 0) return ART_EINVAL;
     if (p->flags & ART_F_ROTATE)
         for (int i = 0; i < 9; ++i)
             if (!std::isfinite(p->rot[i])) return ART_EINVAL;
@@ -106,6 +107,7 @@ int prepare_trace(art_grid* g, const art_params* p, bool adjoint)
     if (ns == 0) return ART_ESTATE;
     const int l0 = p->level0;
     const unsigned npix0 = 12u << (2 * l0);
+    if ((unsigned long long)ns * npix0 >= (1ull << 31)) return ART_EINVAL;  // 32-bit ray slots
     // --- sources: cell-unit positions as df, base-ray luminosity, l_max
     std::vector<SrcDev> hs(ns);
     int lmax_glob = l0;
@@ -269,7 +271,6 @@ TraceArgs make_args(art_grid* g, const art_params* p)
     A.stats = g->d_stats;
     double ws = p->wait_limit_s == 0.0 ? kDefaultWaitS : p->wait_limit_s;
     A.wait_ns = ws < 0.0 ? -1 : (long long)(ws * 1e9);
-    A.l2_hints = p->l2_hints;
     return A;
 }
 
@@ -483,6 +484,7 @@ void art_destroy_grid(art_grid* g)
     dev_free(g->d_sched);
     dev_free(g->d_stats);
     dev_free(g->d_srcL);
+    dev_free(g->d_rec);
     dev_free(g->d_dL_scratch);
     for (int l = 0; l < kNL; ++l) {
         dev_free(g->dir[l]);

@@ -139,6 +139,7 @@ struct TraceArgs {
     float tau_max;
     const float* chi;        // opacity per cell times dx (per cell length)
     const float* chiH;       // neutral-H part of chi (adjoint only)
+    const float4* rec;       // adjoint: per cell {chi, chi_H, w, 0}
     const float* w;          // adjoint weights per cell
     float* grad;             // adjoint output per cell
     double* dL;              // adjoint output per source
@@ -149,7 +150,6 @@ struct TraceArgs {
     Sched* sched;
     DevStats* stats;
     long long wait_ns;       // bound of a grid-barrier wait (<0: give up at once)
-    int l2_hints;            // see art_params.l2_hints
     float gscale;            // adjoint: sigma_H * dx / dV (gamma per unit G)
     const float* srcL;       // adjoint: source luminosities (gradients scale with them)
 };
@@ -157,54 +157,20 @@ struct TraceArgs {
 enum : int { EV_NONE = 0, EV_EXIT = 1, EV_DROP = 2, EV_SPLIT = 3 };
 
 // ---------------------------------------------------------------------------------------
-// memory access with an optional L2 eviction priority
-// ---------------------------------------------------------------------------------------
-struct MemPolicy {
-    unsigned long long gather, deposit;  // createpolicy values
-    bool hint_gather, hint_deposit;
-};
-
-__device__ __forceinline__ MemPolicy make_policy(int mode)
-{
-    MemPolicy m;
-    unsigned long long last, first;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(last));
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(first));
-    m.gather = last;
-    m.deposit = mode == 3 ? first : last;
-    m.hint_gather = mode >= 1;
-    m.hint_deposit = mode >= 2;
-    return m;
-}
-
-__device__ __forceinline__ float load_gather(const float* p, const MemPolicy& m)
-{
-    if (m.hint_gather) {
-        float v;
-        asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(m.gather));
-        return v;
-    }
-    return __ldg(p);
-}
-
-__device__ __forceinline__ void red_v4(float4* q, float4 v, const MemPolicy& m)
-{
-    float* p = reinterpret_cast<float*>(q);
-    if (m.hint_deposit) {
-        asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p),
-                     "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(m.deposit)
-                     : "memory");
-    } else {
-        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x),
-                     "f"(v.y), "f"(v.z), "f"(v.w)
-                     : "memory");
-    }
-}
-
-// ---------------------------------------------------------------------------------------
 // ray walk
 // ---------------------------------------------------------------------------------------
-struct Walk {
+// Per-cell record gathered at every step: the opacity alone (forward), or
+// {opacity, its neutral-H part, loss weight, unused} (adjoint).
+__device__ __forceinline__ float chi_of(const float& c) { return c; }
+__device__ __forceinline__ float chi_of(const float4& c) { return c.x; }
+__device__ __forceinline__ float load_cell(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float4 load_cell(const float4* p) { return __ldg(p); }
+template <class Cell> __device__ __forceinline__ Cell cell_zero();
+template <> __device__ __forceinline__ float cell_zero<float>() { return 0.f; }
+template <> __device__ __forceinline__ float4 cell_zero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+
+template <class Cell>
+struct WalkT {
     df t[3];      // distance from the source to the next face on each axis
     df d[3];      // distance between consecutive faces on each axis (1/|n_a|)
     df tc;        // distance of the current position
@@ -212,13 +178,15 @@ struct Walk {
     int rem[3];   // cells left on each axis before the ray leaves the grid
     float n[3];   // direction (hi parts) for momentum deposits
     float L, tau;
-    float chi;    // opacity of the current cell (prefetched)
+    Cell cell;    // record of the current cell (prefetched)
 };
+using Walk = WalkT<float>;
 
 // Sets up the walk of a ray with direction n and reciprocal inv (df, from the direction
 // table) from source position u (df) starting at radius r0. Returns false if the start
 // point lies outside the grid.
-__device__ __forceinline__ bool walk_start(Walk& W, int nx, int ny, int nz, const df u[3],
+template <class Cell>
+__device__ __forceinline__ bool walk_start(WalkT<Cell>& W, int nx, int ny, int nz, const df u[3],
                                            const df n[3], const df inv[3], df r0)
 {
     const int N[3] = {nx, ny, nz};
@@ -290,10 +258,9 @@ __device__ __forceinline__ df df_sel(bool c, df a, df b) { return {c ? a.hi : b.
 // (when the ray splits at all). The common case (one axis crossing) runs without branches;
 // faces crossed together (ties) take a short side path. When the step ends the ray (event
 // other than EV_NONE) the walk state other than L and tau is left unspecified.
-template <bool kCountOnly>
-__device__ __forceinline__ StepOut walk_step(Walk& W, bool splits, df rmax, int sy, int sz,
-                                             const float* __restrict__ chi_arr, float tau_max,
-                                             const MemPolicy& mp)
+template <bool kCountOnly, class Cell>
+__device__ __forceinline__ StepOut walk_step(WalkT<Cell>& W, bool splits, df rmax, int sy, int sz,
+                                             const Cell* __restrict__ cells, float tau_max)
 {
     StepOut o;
     // earliest face crossing (lexicographic order of the normalised df values)
@@ -315,11 +282,11 @@ __device__ __forceinline__ StepOut walk_step(Walk& W, bool splits, df rmax, int 
                      (m2 ? (W.n[2] > 0.f ? sz : -sz) : 0);
     const bool out = (m0 && W.rem[0] == 0) || (m1 && W.rem[1] == 0) || (m2 && W.rem[2] == 0);
     const bool go = !split && !out;
-    const float nchi = go ? load_gather(chi_arr + nidx, mp) : 0.f;  // prefetch for the next step
+    const Cell ncell = go ? load_cell(cells + nidx) : cell_zero<Cell>();  // prefetch
     // deposit in the current cell (segments of length <= 0 deposit nothing)
     const bool seg = o.ds > 0.f;
     const float ds = seg ? o.ds : 0.f;
-    const float x = W.chi * ds;
+    const float x = chi_of(W.cell) * ds;
     o.cell = seg ? W.idx : -1;
     o.Lin = W.L;
     o.dtau = x;
@@ -353,7 +320,7 @@ __device__ __forceinline__ StepOut walk_step(Walk& W, bool splits, df rmax, int 
     }
     W.tc = tm;
     W.idx = nidx;
-    W.chi = nchi;
+    W.cell = ncell;
     return o;
 }
 
@@ -361,8 +328,15 @@ __device__ __forceinline__ StepOut walk_step(Walk& W, bool splits, df rmax, int 
 // order) and issues one reduction per run. Used only for the first segment of base-level
 // rays, which all start in their source's cell: at l0 = 8 that is 786,432 deposits into one
 // cell per source, whose FP32 sum the merge keeps accurate. Warp-uniform.
-__device__ __forceinline__ void deposit_merged(float4* __restrict__ acc, int cell, float4 v,
-                                               const MemPolicy& mp)
+__device__ __forceinline__ void red_v4(float4* q, float4 v)
+{
+    float* p = reinterpret_cast<float*>(q);
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ void deposit_merged(float4* __restrict__ acc, int cell, float4 v)
 {
     const unsigned lane = threadIdx.x & 31u;
     const int prev = __shfl_up_sync(kFull, cell, 1);
@@ -380,15 +354,14 @@ __device__ __forceinline__ void deposit_merged(float4* __restrict__ acc, int cel
             v.x += ox; v.y += oy; v.z += oz; v.w += ow;
         }
     }
-    if (cell >= 0 && !dup) red_v4(acc + cell, v, mp);
+    if (cell >= 0 && !dup) red_v4(acc + cell, v);
 }
 
 // One 16-byte vector reduction (G, dL n) into the accumulator of `cell` (none if < 0).
 // Merging equal cells across lanes first was measured slower than letting L2 combine them.
-__device__ __forceinline__ void deposit(float4* __restrict__ acc, int cell, float4 v,
-                                        const MemPolicy& mp)
+__device__ __forceinline__ void deposit(float4* __restrict__ acc, int cell, float4 v)
 {
-    if (cell >= 0) red_v4(acc + cell, v, mp);
+    if (cell >= 0) red_v4(acc + cell, v);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -422,13 +395,21 @@ __device__ __forceinline__ void tally_flush(const Tally& T, DevStats* st)
     }
 }
 
+// Slot value of a ray buffer entry that holds no ray: the children slots of a parent that
+// did not split (each parent owns four consecutive child slots, so fronts keep pixel order).
+constexpr unsigned kHole = 0xffffffffu;
+
 // Starts the walk of ray i of level l: loads its record, its source and its direction
-// entry. Returns true if the ray starts inside the grid. L0 receives its entering L.
-__device__ __forceinline__ bool ray_begin(const TraceArgs& A, const LevelInfo& LV, const RayBuf& B,
-                                          int l, unsigned long long i, Walk& W, unsigned& s,
-                                          unsigned& p, float& L0, bool& splits)
+// entry. Returns 1 if the ray starts inside the grid, 0 if it starts outside (it escapes at
+// once), -1 if slot i holds no ray. L0 receives its entering L.
+template <class Cell>
+__device__ __forceinline__ int ray_begin(const TraceArgs& A, const LevelInfo& LV, const RayBuf& B,
+                                         int l, unsigned long long i, WalkT<Cell>& W,
+                                         const Cell* cells, unsigned& s, unsigned& p, float& L0,
+                                         bool& splits)
 {
     s = __ldcg(B.src + i);
+    if (s == kHole) return -1;
     p = __ldcg(B.pix + i);
     const float4 sh = __ldg(&A.src[s].hi);
     const float4 sl = __ldg(&A.src[s].lo);
@@ -444,8 +425,27 @@ __device__ __forceinline__ bool ray_begin(const TraceArgs& A, const LevelInfo& L
     const bool inside = walk_start(W, A.nx, A.ny, A.nz, u, n, inv, LV.r0);
     W.L = L0;
     W.tau = tau0;
-    W.chi = inside ? __ldg(A.chi + W.idx) : 0.f;
-    return inside;
+    W.cell = inside ? __ldg(cells + W.idx) : cell_zero<Cell>();
+    return inside ? 1 : 0;
+}
+
+// Marks the four child slots of parent slot c4/4 as empty.
+__device__ __forceinline__ void write_holes(const RayBuf& C, unsigned long long c4)
+{
+    if (c4 + 4 <= C.cap)
+        *reinterpret_cast<uint4*>(C.src + c4) = make_uint4(kHole, kHole, kHole, kHole);
+}
+
+// Adds a warp's count of rays started at level l to the per-level counters.
+__device__ __forceinline__ void count_rays(DevStats* st, int l, unsigned n)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) n += __shfl_down_sync(kFull, n, off);
+    if ((threadIdx.x & 31u) == 0 && n > 0) {
+        atomicAdd(&st->rays_per_level[l], (unsigned long long)n);
+        atomicAdd(&st->rays_total, (unsigned long long)n);
+        atomicMax(&st->level_reached, l);
+    }
 }
 
 // Grid-wide barrier for a cooperative launch. Every wait is bounded by wait_ns of

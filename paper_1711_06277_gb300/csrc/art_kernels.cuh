@@ -144,32 +144,36 @@ __global__ void k_inject(int s0, int nsrc, unsigned npix0, RayBuf B, unsigned lo
     B.tau[i] = 0.f;
 }
 
-// Processes rays [cursor .. end) of level l (cursor advanced atomically by warps, `chunk`
-// rays at a time). Idle lanes are refilled once at least a quarter of the warp is idle, so
-// the ray set-up runs with many lanes at once. Warp-uniform: every lane of the warp must
-// call it.
+// Processes the rays in slots [cursor .. end) of level l, whose phase starts at slot
+// `begin` (cursor advanced atomically by warps, `chunk` slots at a time). The children of
+// the ray in slot i go to slots 4 (i - begin) .. +3 of level l + 1, so the next front keeps
+// the pixel order of this one; parents that do not split mark their four slots empty. Idle
+// lanes are refilled once at least a quarter of the warp is idle, so the ray set-up runs
+// with many lanes at once. Warp-uniform: every lane of the warp must call it.
 __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
-                         unsigned long long end, Tally& T)
+                         unsigned long long begin, unsigned long long end, Tally& T)
 {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt = (1u << lane) - 1u;
     const LevelInfo LV = A.levels[l];
     const RayBuf B = A.buf[l];
     const RayBuf C = A.buf[l + 1];
-    unsigned long long* child_count = &A.sched->count[l + 1];
+    const bool has_next = l < A.lmax_glob;
     const int sy = A.nx, sz = A.nx * A.ny;
-    const MemPolicy mp = make_policy(A.l2_hints);
 
-    unsigned long long wnext = 0, wend = 0;
+    // slot indices fit in 32 bits (level buffers hold fewer than 2^31 slots)
+    const unsigned b32 = (unsigned)begin, e32 = (unsigned)end;
+    unsigned wnext = 0, wend = 0;
     bool more = true;
     bool active = false;
     Walk W;
     unsigned s = 0, p = 0;
+    unsigned slot = 0;
     float L0 = 0.f;
     bool splits = false;
     bool first = false;  // next step is the first segment of a base-level ray
     const bool base = l == A.level0;
-    unsigned ncross = 0;
+    unsigned ncross = 0, nrays = 0;
 
     for (;;) {
         // refill idle lanes from the warp's chunk, fetching chunks as needed
@@ -181,18 +185,25 @@ __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
                     if (lane == 0) b = atomicAdd(cursor, (unsigned long long)A.chunk);
                     b = __shfl_sync(kFull, b, 0);
                     if (b >= end) { more = false; break; }
-                    wnext = b;
-                    wend = min(b + (unsigned long long)A.chunk, end);
+                    wnext = (unsigned)b;
+                    wend = min(wnext + (unsigned)A.chunk, e32);
                 }
-                const unsigned avail = (unsigned)min(wend - wnext, 32ull);
+                const unsigned avail = min(wend - wnext, 32u);
                 const unsigned rank = __popc(need & lt);
                 if (!active && rank < avail) {
-                    if (ray_begin(A, LV, B, l, wnext + rank, W, s, p, L0, splits)) {
+                    slot = wnext + rank;
+                    const int st = ray_begin(A, LV, B, l, slot, W, A.chi, s, p, L0, splits);
+                    if (st > 0) {
                         active = true;
                         first = base;
-                    } else {  // starts outside the grid: escapes with its full luminosity
-                        T.escaped += (double)L0;
-                        T.destroy += LV.destroy_w;
+                        ++nrays;
+                    } else {
+                        if (st == 0) {  // starts outside the grid: escapes with its full L
+                            T.escaped += (double)L0;
+                            T.destroy += LV.destroy_w;
+                            ++nrays;
+                        }
+                        if (has_next) write_holes(C, 4ull * (slot - b32));
                     }
                 }
                 wnext += min(avail, (unsigned)__popc(need));
@@ -204,13 +215,12 @@ __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
             continue;
         }
 
-        bool want_split = false;
 #pragma unroll 1
         for (int k = 0; k < 4; ++k) {
             int cell = -1;
             float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
             if (active) {
-                const StepOut o = walk_step<false>(W, splits, LV.rmax, sy, sz, A.chi, A.tau_max, mp);
+                const StepOut o = walk_step<false>(W, splits, LV.rmax, sy, sz, A.chi, A.tau_max);
                 if (o.cell >= 0) {
                     cell = o.cell;
                     dv = make_float4(o.G, o.dL * W.n[0], o.dL * W.n[1], o.dL * W.n[2]);
@@ -218,58 +228,45 @@ __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
                 }
                 if (o.ev != EV_NONE) {
                     active = false;
+                    const unsigned long long c4 = 4ull * (slot - b32);
                     if (o.ev == EV_SPLIT) {
-                        want_split = true;
+                        if (c4 + 4 <= C.cap) {
+                            const float Lc = 0.25f * W.L;
+                            *reinterpret_cast<uint4*>(C.src + c4) = make_uint4(s, s, s, s);
+                            *reinterpret_cast<uint4*>(C.pix + c4) =
+                                make_uint4(4 * p, 4 * p + 1, 4 * p + 2, 4 * p + 3);
+                            *reinterpret_cast<float4*>(C.L + c4) = make_float4(Lc, Lc, Lc, Lc);
+                            *reinterpret_cast<float4*>(C.tau + c4) =
+                                make_float4(W.tau, W.tau, W.tau, W.tau);
+                        } else {
+                            atomicCAS(&A.stats->error, 0, -3);  // ART_EQUEUE_OVERFLOW
+                        }
                     } else {
                         if (o.ev == EV_EXIT) T.escaped += (double)W.L;
                         else T.dropped += (double)W.L;
                         T.destroy += LV.destroy_w;
+                        if (has_next) write_holes(C, c4);
                     }
                 }
             }
-            if (base && __any_sync(kFull, first)) deposit_merged(A.acc, cell, dv, mp);
-            else deposit(A.acc, cell, dv, mp);
+            if (base && __any_sync(kFull, first)) deposit_merged(A.acc, cell, dv);
+            else deposit(A.acc, cell, dv);
             first = false;
-        }
-        // append the children of split rays to the next level
-        const unsigned sm = __ballot_sync(kFull, want_split);
-        if (sm) {
-            unsigned long long base = 0;
-            const int leader = __ffs(sm) - 1;
-            if ((int)lane == leader) base = atomicAdd(child_count, 4ull * __popc(sm));
-            base = __shfl_sync(kFull, base, leader);
-            if (want_split) {
-                unsigned long long slot = base + 4ull * __popc(sm & lt);
-                if (slot + 4 <= C.cap) {
-                    const float Lc = 0.25f * W.L;
-                    *reinterpret_cast<uint4*>(C.src + slot) = make_uint4(s, s, s, s);
-                    *reinterpret_cast<uint4*>(C.pix + slot) =
-                        make_uint4(4 * p, 4 * p + 1, 4 * p + 2, 4 * p + 3);
-                    *reinterpret_cast<float4*>(C.L + slot) = make_float4(Lc, Lc, Lc, Lc);
-                    *reinterpret_cast<float4*>(C.tau + slot) =
-                        make_float4(W.tau, W.tau, W.tau, W.tau);
-                } else {
-                    atomicCAS(&A.stats->error, 0, -3);  // ART_EQUEUE_OVERFLOW
-                }
-            }
         }
     }
     T.crossings += ncross;
+    count_rays(A.stats, l, nrays);
 }
 
-// Plain schedule: all rays of level l currently in its buffer.
+// Plain schedule: all slots of level l (one source's front).
 __global__ void __launch_bounds__(512, 2) k_trace_level(const __grid_constant__ TraceArgs A, int l)
 {
     Tally T = {0.0, 0.0, 0ull, 0ull};
     // a front that overflowed (status set by the writer) is cut at the buffer capacity
     const unsigned long long end =
         min(*((volatile unsigned long long*)&A.sched->count[l]), A.buf[l].cap);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && end > 0) {
-        atomicAdd(&A.stats->rays_per_level[l], end);
-        atomicAdd(&A.stats->rays_total, end);
-        atomicMax(&A.stats->level_reached, l);
-    }
-    run_rays(A, l, &A.sched->cursor[l], end, T);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && l < A.lmax_glob) A.sched->count[l + 1] = 4 * end;
+    run_rays(A, l, &A.sched->cursor[l], 0, end, T);
     tally_flush(T, A.stats);
 }
 
@@ -286,7 +283,7 @@ __global__ void __launch_bounds__(512, 2) k_trace_persistent(const __grid_consta
     Tally T = {0.0, 0.0, 0ull, 0ull};
     Sched* sc = A.sched;
     __shared__ int s_level;
-    __shared__ unsigned long long s_end;
+    __shared__ unsigned long long s_begin, s_end;
     for (;;) {
         if (!grid_barrier(sc, A.stats, A.wait_ns)) break;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -305,9 +302,7 @@ __global__ void __launch_bounds__(512, 2) k_trace_persistent(const __grid_consta
                 sc->phase_end = have;
                 sc->cursor[l] = have - take;
                 cnt[l] = have - take;
-                A.stats->rays_per_level[l] += take;
-                A.stats->rays_total += take;
-                if (l > A.stats->level_reached) A.stats->level_reached = l;
+                if (l < A.lmax_glob) cnt[l + 1] = 4 * take;  // the children's slots
             }
             __threadfence();
         }
@@ -315,12 +310,13 @@ __global__ void __launch_bounds__(512, 2) k_trace_persistent(const __grid_consta
         if (threadIdx.x == 0) {
             volatile Sched* v = sc;
             s_level = v->done ? -1 : v->phase_level;
+            s_begin = v->phase_begin;
             s_end = v->phase_end;
         }
         __syncthreads();
         const int l = s_level;
         if (l < 0) break;
-        run_rays(A, l, &sc->cursor[l], s_end, T);
+        run_rays(A, l, &sc->cursor[l], s_begin, s_end, T);
     }
     tally_flush(T, A.stats);
 }

@@ -41,11 +41,11 @@ def _oracle(nH0, pos, L, dx, p, nH=None, threads=8):
     return O.trace(prob, nthreads=threads)
 
 
-def _check(res, ref, nH0, p, nH=None, exact_counts=True, force_rel=PA.REL):
+def _check(res, ref, nH0, p, nH=None, exact_counts=True, force_rel=PA.REL, gamma_rel=PA.REL):
     st = res["stats"]
     assert st["status"] == 0
-    PA.compare_field(res["gamma"], ref.gamma, what="gamma")
-    PA.compare_field(res["energy"], ref.energy, what="energy")
+    PA.compare_field(res["gamma"], ref.gamma, rel=gamma_rel, what="gamma")
+    PA.compare_field(res["energy"], ref.energy, rel=gamma_rel, what="energy")
     chi = nH0.astype(np.float32).astype(np.float64) * p.sigma_H
     if nH is not None:
         chi = chi + nH.astype(np.float32).astype(np.float64) * p.sigma_d
@@ -151,9 +151,9 @@ def test_odd_shapes_and_levels(art, shape, level0, lmax):
                      level_cap=lmax, tau_max=30.0)
     ref = O.trace(prob, nthreads=8)
     # At l0 = 8 every cell near a source receives ~10^5-10^6 deposits; FP32 summation noise
-    # of the cancelling force components grows like sqrt(n) eps relative to chi E.
+    # grows like sqrt(n) eps (relative to chi E for the cancelling force components).
     _check(res, ref, rho, p, exact_counts=ref.near_tie_rays == 0,
-           force_rel=1e-4 if level0 == 8 else PA.REL)
+           force_rel=1e-4 if level0 == 8 else PA.REL, gamma_rel=5e-5 if level0 == 8 else PA.REL)
 
 
 def test_source_near_faces_and_small_tau_max(art):
