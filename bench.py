@@ -381,6 +381,8 @@ def main():
     ap.add_argument("--no-tune", dest="tune", action="store_false")
     ap.add_argument("--adjoint", action="store_true", default=True)
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="only the forward/backward timing of the 128^3 / 16-source case")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-plain", action="store_true", default=True)
     ap.add_argument("--no-compare-plain", dest="compare_plain", action="store_false")
@@ -411,6 +413,13 @@ def main():
                 "e2e": {"value": r["value"], "unit": "crossings/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
+        return
+
+    if args.adjoint_only:
+        if rank == 0:
+            import torch
+            from paper_1711_06277_gb300 import art as A
+            print(json.dumps({"adjoint": adjoint_ratio(A, torch.device("cuda", local_rank))}))
         return
 
     if world > 1:
