@@ -53,25 +53,21 @@ __device__ __forceinline__ float dphi_of(float x, float em)
     return ((1.f + x) * (1.f + em) - 1.f) / (x * x);
 }
 
+// Per-lane sum of dloss/dL for the source of the lane's recent rays, flushed to the global
+// FP64 sum when the lane moves to another source (rays of one source are consecutive).
 struct DLacc {
-    double v;
+    df v;
     unsigned src;
 };
 
-__device__ __forceinline__ void dl_add(DLacc& D, double* dL, unsigned s, double own)
+__device__ __forceinline__ void dl_add(DLacc& D, double* dL, unsigned s, df own)
 {
     if (s != D.src) {
-        if (D.src != 0xffffffffu && D.v != 0.0) atomicAdd(dL + D.src, D.v);
+        if (D.src != 0xffffffffu && D.v.hi != 0.f) atomicAdd(dL + D.src, (double)D.v.hi + (double)D.v.lo);
         D.src = s;
-        D.v = 0.0;
+        D.v = {0.f, 0.f};
     }
-    D.v += own;
-}
-
-__device__ __forceinline__ df df_of(double v)
-{
-    const float h = __double2float_rn(v);
-    return {h, __double2float_rn(v - (double)h)};
+    D.v = df_add(D.v, own);
 }
 
 // One phase of the reverse sweep on rays [cursor .. end) of level l. Warp-uniform.
@@ -87,7 +83,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
     const bool has_next = l < A.lmax_glob;
     const float gs = A.gscale;
     const int sy = A.nx, sz = A.nx * A.ny;
-    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    const float2 nan2 = make_float2(__int_as_float(0x7fc00000), 0.f);
 
     // slot indices fit in 32 bits (level buffers hold fewer than 2^31 slots)
     const unsigned b32 = (unsigned)begin, e32 = (unsigned)end;
@@ -99,7 +95,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
     unsigned slot = 0;
     float L0 = 0.f, Ls = 0.f;
     df own = {0.f, 0.f};   // own weighted sum (pass 1), kept for dL in pass 2
-    double total = 0.0;    // own + descendants (pass 2)
+    float total = 0.f;     // own + descendants (pass 2), passed to the parent
     df rem = {0.f, 0.f};   // weighted sum over what follows the current segment (pass 2)
     bool splits = false;
     unsigned ncross = 0, nrays = 0;
@@ -132,15 +128,15 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
                             T.destroy += LV.destroy_w;
                             ++nrays;
                         }
-                        B.own[slot] = nan;
+                        B.own[slot] = nan2;
                         if (has_next) write_holes(C, 4ull * (slot - b32));
                     }
                 } else {
-                    const double ov = __ldcg(B.own + slot);
-                    if (ov == ov) {  // a split ray waiting for its collapse
-                        total = ov + __ldcg(B.sub + slot);
-                        own = df_of(ov);
-                        rem = df_of(total);
+                    const float2 ov = __ldcg(B.own + slot);
+                    if (ov.x == ov.x) {  // a split ray waiting for its collapse
+                        own = {ov.x, ov.y};
+                        rem = df_add(own, {__ldcg(B.sub + slot), 0.f});
+                        total = rem.hi + rem.lo;
                         ray_begin(A, LV, B, l, slot, W, A.rec, s, p, L0, splits);
                         Ls = __ldg(A.srcL + s);
                         mode = 2;
@@ -177,8 +173,8 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
                     if (mode == 1) {
                         const unsigned long long c4 = 4ull * (slot - b32);
                         if (o.ev == EV_SPLIT) {
-                            B.own[slot] = (double)own.hi + (double)own.lo;
-                            B.sub[slot] = 0.0;
+                            B.own[slot] = make_float2(own.hi, own.lo);
+                            B.sub[slot] = 0.f;
                             if (c4 + 4 <= C.cap) {
                                 const float Lc = 0.25f * W.L;
                                 const unsigned ps = (unsigned)slot;
@@ -198,15 +194,15 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
                             else T.dropped += (double)W.L;
                             T.destroy += LV.destroy_w;
                             if (has_next) write_holes(C, c4);
-                            B.own[slot] = nan;  // finished within this phase
-                            total = (double)own.hi + (double)own.lo;
+                            B.own[slot] = nan2;  // finished within this phase
+                            total = own.hi + own.lo;
                             rem = own;
                             ray_begin(A, LV, B, l, slot, W, A.rec, s, p, L0, splits);
                             mode = 2;
                         }
                     } else {
                         if (l > A.level0) atomicAdd(P.sub + __ldcg(B.parent + slot), total);
-                        dl_add(D, A.dL, s, (double)own.hi + (double)own.lo);
+                        dl_add(D, A.dL, s, own);
                         mode = 0;
                     }
                 }
@@ -221,7 +217,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
 __global__ void __launch_bounds__(256, 3) k_backward_persistent(const __grid_constant__ TraceArgs A)
 {
     Tally T = {0.0, 0.0, 0ull, 0ull};
-    DLacc D = {0.0, 0xffffffffu};
+    DLacc D = {{0.f, 0.f}, 0xffffffffu};
     Sched* sc = A.sched;
     __shared__ int s_level, s_kind;
     __shared__ unsigned long long s_begin, s_end;
@@ -274,7 +270,7 @@ __global__ void __launch_bounds__(256, 3) k_backward_persistent(const __grid_con
         if (l < 0) break;
         run_adjoint(A, l, s_kind, &sc->cursor[l], s_begin, s_end, T, D);
     }
-    if (D.src != 0xffffffffu && D.v != 0.0) atomicAdd(A.dL + D.src, D.v);
+    if (D.src != 0xffffffffu && D.v.hi != 0.f) atomicAdd(A.dL + D.src, (double)D.v.hi + (double)D.v.lo);
     tally_flush(T, A.stats);
 }
 

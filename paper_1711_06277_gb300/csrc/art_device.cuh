@@ -100,8 +100,8 @@ struct RayBuf {
     float* tau;
     // adjoint extras (NULL in forward traces)
     unsigned* parent;   // slot of the parent in the level above
-    double* own;        // weighted sum over the ray's own segments (pass 1)
-    double* sub;        // weighted sum over the ray's descendants (filled by the children)
+    float2* own;        // weighted sum over the ray's own segments (pass 1), double-float
+    float* sub;         // weighted sum over the ray's descendants (added by the children)
     unsigned long long cap;
 };
 
@@ -263,24 +263,51 @@ __device__ __forceinline__ StepOut walk_step(WalkT<Cell>& W, bool splits, df rma
                                              const Cell* __restrict__ cells, float tau_max)
 {
     StepOut o;
-    // earliest face crossing (lexicographic order of the normalised df values)
-    const bool c01 = df_le(W.t[0], W.t[1]);
-    df tm = df_sel(c01, W.t[0], W.t[1]);
-    int a = c01 ? 0 : 1;
-    const bool c2 = df_le(tm, W.t[2]);
-    tm = df_sel(c2, tm, W.t[2]);
-    a = c2 ? a : 2;
-    const bool split = splits && df_le(rmax, tm);
+    // Earliest face crossing, decided on the hi parts: for normalised df values |lo| is at
+    // most half an ulp of hi, so distinct hi parts order the values exactly and no two of
+    // them can lie within the 1e-12 tie tolerance. Equal hi parts (exact ties, near ties, a
+    // face at the split radius) take the exact double-float path below.
+    const float h0 = W.t[0].hi, h1 = W.t[1].hi, h2 = W.t[2].hi;
+    const bool c01 = h0 < h1;
+    const float h01 = c01 ? h0 : h1;
+    const bool c2 = h01 < h2;
+    int a = c2 ? (c01 ? 0 : 1) : 2;
+    const float hm = c2 ? h01 : h2;
+    df tm = df_sel(a == 0, W.t[0], df_sel(a == 1, W.t[1], W.t[2]));
+    bool split = splits && rmax.hi < hm;
+    bool m0 = a == 0, m1 = a == 1, m2 = a == 2;
+    bool single = true;
+    if (h0 == h1 || h0 == h2 || h1 == h2 || (splits && rmax.hi == hm)) {
+        const bool e01 = df_le(W.t[0], W.t[1]);
+        tm = df_sel(e01, W.t[0], W.t[1]);
+        a = e01 ? 0 : 1;
+        if (!df_le(tm, W.t[2])) {
+            tm = W.t[2];
+            a = 2;
+        }
+        split = splits && df_le(rmax, tm);
+        // axes crossing together with the earliest one (relative tie 1e-12): a diagonal step
+        const float tol = 1e-12f * tm.hi;
+        m0 = df_diff(W.t[0], tm) <= tol;
+        m1 = df_diff(W.t[1], tm) <= tol;
+        m2 = df_diff(W.t[2], tm) <= tol;
+        single = (int)m0 + (int)m1 + (int)m2 == 1;
+    }
     o.ds = df_diff(split ? rmax : tm, W.tc);
-    // axes crossing together with the earliest one (relative tie 1e-12): a diagonal step
-    const float tol = 1e-12f * tm.hi;
-    const bool m0 = df_diff(W.t[0], tm) <= tol;
-    const bool m1 = df_diff(W.t[1], tm) <= tol;
-    const bool m2 = df_diff(W.t[2], tm) <= tol;
     // next cell and whether it leaves the grid
-    const int nidx = W.idx + (m0 ? (W.n[0] > 0.f ? 1 : -1) : 0) + (m1 ? (W.n[1] > 0.f ? sy : -sy) : 0) +
-                     (m2 ? (W.n[2] > 0.f ? sz : -sz) : 0);
-    const bool out = (m0 && W.rem[0] == 0) || (m1 && W.rem[1] == 0) || (m2 && W.rem[2] == 0);
+    int nidx = W.idx;
+    bool out;
+    if (single) {
+        const float na = a == 0 ? W.n[0] : (a == 1 ? W.n[1] : W.n[2]);
+        const int st = a == 0 ? 1 : (a == 1 ? sy : sz);
+        const int r = a == 0 ? W.rem[0] : (a == 1 ? W.rem[1] : W.rem[2]);
+        nidx += na > 0.f ? st : -st;
+        out = r == 0;
+    } else {
+        nidx += (m0 ? (W.n[0] > 0.f ? 1 : -1) : 0) + (m1 ? (W.n[1] > 0.f ? sy : -sy) : 0) +
+                (m2 ? (W.n[2] > 0.f ? sz : -sz) : 0);
+        out = (m0 && W.rem[0] == 0) || (m1 && W.rem[1] == 0) || (m2 && W.rem[2] == 0);
+    }
     const bool go = !split && !out;
     const Cell ncell = go ? load_cell(cells + nidx) : cell_zero<Cell>();  // prefetch
     // deposit in the current cell (segments of length <= 0 deposit nothing)
@@ -313,7 +340,7 @@ __device__ __forceinline__ StepOut walk_step(WalkT<Cell>& W, bool splits, df rma
     W.rem[0] -= m0 ? 1 : 0;
     W.rem[1] -= m1 ? 1 : 0;
     W.rem[2] -= m2 ? 1 : 0;
-    if ((int)m0 + (int)m1 + (int)m2 > 1) {
+    if (!single) {
         if (m0 && a != 0) W.t[0] = df_add(W.t[0], W.d[0]);
         if (m1 && a != 1) W.t[1] = df_add(W.t[1], W.d[1]);
         if (m2 && a != 2) W.t[2] = df_add(W.t[2], W.d[2]);
