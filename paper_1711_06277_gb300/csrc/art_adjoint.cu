@@ -178,9 +178,11 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
                             if (c4 + 4 <= C.cap) {
                                 const float Lc = 0.25f * W.L;
                                 const unsigned ps = (unsigned)slot;
-                                *reinterpret_cast<uint4*>(C.src + c4) = make_uint4(s, s, s, s);
+                                const unsigned rs = __ldcg(B.src + slot);  // reloaded: not kept live
+                                const unsigned rp = __ldcg(B.pix + slot);
+                                *reinterpret_cast<uint4*>(C.src + c4) = make_uint4(rs, rs, rs, rs);
                                 *reinterpret_cast<uint4*>(C.pix + c4) =
-                                    make_uint4(4 * p, 4 * p + 1, 4 * p + 2, 4 * p + 3);
+                                    make_uint4(4 * rp, 4 * rp + 1, 4 * rp + 2, 4 * rp + 3);
                                 *reinterpret_cast<float4*>(C.L + c4) = make_float4(Lc, Lc, Lc, Lc);
                                 *reinterpret_cast<float4*>(C.tau + c4) =
                                     make_float4(W.tau, W.tau, W.tau, W.tau);
@@ -202,7 +204,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
                         }
                     } else {
                         if (l > A.level0) atomicAdd(P.sub + __ldcg(B.parent + slot), total);
-                        dl_add(D, A.dL, s, own);
+                        dl_add(D, A.dL, __ldcg(B.src + slot), own);
                         mode = 0;
                     }
                 }
@@ -214,7 +216,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
     count_rays(A.stats, l, nrays);
 }
 
-__global__ void __launch_bounds__(256, 3) k_backward_persistent(const __grid_constant__ TraceArgs A)
+__global__ void __launch_bounds__(256, 4) k_backward_persistent(const __grid_constant__ TraceArgs A)
 {
     Tally T = {0.0, 0.0, 0ull, 0ull};
     DLacc D = {{0.f, 0.f}, 0xffffffffu};
