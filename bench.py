@@ -47,6 +47,33 @@ CONFIGS = {
 }
 
 
+def kernel_sources_digest() -> str:
+    """SHA-256 over the CUDA sources, to tell whether a stored ncu capture still applies."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1711_06277_gb300", "csrc")
+    for path in sorted(glob.glob(os.path.join(csrc, "*.cu*")) + glob.glob(os.path.join(csrc, "*.h"))):
+        with open(path, "rb") as f:
+            h.update(os.path.basename(path).encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def captured_traffic(crossings_per_launch: float):
+    """DRAM bytes of one trace launch, scaled from the committed ncu capture of a smaller case
+    of the same workload (bytes per crossing x crossings); None if the kernels changed since."""
+    path = os.path.join(ROOT, "profiles", "trace_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None, "no capture"
+    if d.get("sources_sha256") != kernel_sources_digest():
+        return None, "kernel changed since the capture"
+    per = float(d["dram_bytes"]) / float(d["crossings"])
+    return per * crossings_per_launch, f"scaled from {d['case']} ({per:.2f} B/crossing)"
+
+
 def _measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -209,6 +236,7 @@ def run_ours(args, rank, world, local_rank):
     trace_s = statistics.mean(step_ms) / 1e3
     per_launch_cross = cross / args.steps
     achieved = per_launch_cross * BYTES_PER_CROSSING / trace_s / 1e9
+    traffic, traffic_note = captured_traffic(per_launch_cross)
 
     # end to end through the public API with host buffers (pinned): H2D of the neutral
     # density, trace + update, D2H of the updated neutral fraction
@@ -246,7 +274,8 @@ def run_ours(args, rank, world, local_rank):
     return {
         "value": value, "ms": ms_all, "cross": cross_all, "clocks": clk.summary(),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note,
+                     "peak_kind": peak_kind,
                      "kernel": "k_trace_persistent",
                      "bytes_per_crossing": BYTES_PER_CROSSING,
                      "crossings_per_launch": per_launch_cross,

@@ -57,7 +57,7 @@ typedef struct art_grid art_grid; /* opaque, owned by the library */
 
 /* Trace parameters (Sec. 2.1, Sec. 2.3). Fill with art_params_default, then override. */
 typedef struct {
-    int level0;          /* base HEALPix level l0, 0..8 (paper default 4) */
+    int level0;          /* base HEALPix level l0, 0..12 (paper default 4) */
     int level_max;       /* < 0: per source, the smallest l >= l0 whose r_max reaches the
                             farthest box corner, capped at 13; else a fixed l_max, l0..13 */
     double m_ray;        /* split criterion: rays per cell face (paper default 4) */
@@ -130,7 +130,7 @@ int art_num_sources(const art_grid* g);
  * without it the call only enqueues work and art_get_stats reports later. The first call
  * for a given (l_max, level0, sources) allocates ray buffers and direction tables, so do one
  * untimed call before capturing a stream into a CUDA graph.
- * Errors: ART_EINVAL (bad parameters: level0 outside 0..8, level_max outside l0..13,
+ * Errors: ART_EINVAL (bad parameters: level0 outside 0..12, level_max outside l0..13,
  * m_ray <= 0, tau_max <= 0, sigma < 0, chunk not a multiple of 32, block_threads not a
  * multiple of 32 in 64..1024, queue_capacity < 4), ART_ESTATE (no sources), ART_ENOMEM,
  * ART_ECUDA. */

@@ -399,7 +399,7 @@ static int or_setup(or_problem* P, int nx, int ny, int nz, double dx, const floa
                     double sigma_H, double sigma_d, const double* rot)
 {
     if (nx <= 0 || ny <= 0 || nz <= 0 || !(dx > 0) || !nH0) return -1;
-    if (level0 < 0 || level0 > 8 || !(m_ray > 0) || !(tau_max > 0)) return -1;
+    if (level0 < 0 || level0 > 12 || !(m_ray > 0) || !(tau_max > 0)) return -1;
     if (level_cap >= 0 && (level_cap < level0 || level_cap > OR_MAX_LEVEL)) return -1;
     P->n[0] = nx; P->n[1] = ny; P->n[2] = nz;
     P->dx = dx; P->nH0 = nH0; P->nH = nH;

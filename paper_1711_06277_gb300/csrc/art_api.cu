@@ -77,7 +77,7 @@ namespace art {
 int check_params(const art_params* p)
 {
     if (!p) return ART_EINVAL;
-    if (p->level0 < 0 || p->level0 > 8) return ART_EINVAL;
+    if (p->level0 < 0 || p->level0 > 12) return ART_EINVAL;
     if (p->level_max >= 0 && (p->level_max < p->level0 || p->level_max > ART_MAX_LEVEL))
         return ART_EINVAL;
     if (!(p->m_ray > 0.0) || !std::isfinite(p->m_ray)) return ART_EINVAL;

@@ -34,7 +34,7 @@ def test_no_sources_is_state_error(art):
     assert e.value.status == C.ART_ESTATE
 
 
-@pytest.mark.parametrize("kw", [dict(level0=9), dict(level0=3, level_max=2), dict(m_ray=0.0),
+@pytest.mark.parametrize("kw", [dict(level0=13), dict(level0=3, level_max=2), dict(m_ray=0.0),
                                 dict(tau_max=-1.0), dict(sigma_H=-1.0), dict(chunk=48),
                                 dict(block_threads=100), dict(queue_capacity=2)])
 def test_bad_params(art, kw):
