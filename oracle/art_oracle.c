@@ -180,6 +180,7 @@ typedef struct {
     double m_ray, tau_max;
     double rot[9];
     int use_rot;
+    int two_bin;        /* a second, non-ionizing bin attenuated by dust only (Sec. 2.3) */
     double rmax_unit;   /* sqrt(3/(pi m_ray)): r_max(l) = rmax_unit * 2^l (cells) */
 } or_problem;
 
@@ -189,12 +190,14 @@ typedef struct {
     long long destroy;  /* sum of 4^(lmax_global - l) over retired rays */
     int level_reached;
     double absorbed, escaped, dropped;
+    double absorbed_n, escaped_n, dropped_n;  /* non-ionizing bin (two-bin traces) */
 } or_tally;
 
 typedef struct {
     int level;
     uint64_t pix;
     double L, tau;
+    double Ln, taun;  /* non-ionizing bin (two-bin traces), else 0 */
 } or_ray;
 
 static double or_rmax(const or_problem* P, int level)
@@ -323,12 +326,19 @@ static int or_walk(const or_problem* P, const double u[3], or_ray* ray, int lmax
             double dsp = ds * dx;
             double dtau = chi * dsp;
             double dL = -ray->L * expm1(-dtau);
+            /* non-ionizing bin: chi_n = n_H sigma_d; its momentum adds to the force
+             * (Eq. e:radforce sums chi_nu F_nu / c over the bins) */
+            double dtaun = 0.0, dLn = 0.0;
+            if (P->two_bin) {
+                dtaun = (P->nH ? (double)P->nH[idx] * P->sigma_d : 0.0) * dsp;
+                dLn = -ray->Ln * expm1(-dtaun);
+            }
             if (acc) {
                 double G = ray->L * dsp * or_phi(dtau);
                 or_add(acc + idx, G, atomic);
-                or_add(acc + ncell + idx, dL * n[0], atomic);
-                or_add(acc + 2 * ncell + idx, dL * n[1], atomic);
-                or_add(acc + 3 * ncell + idx, dL * n[2], atomic);
+                or_add(acc + ncell + idx, (dL + dLn) * n[0], atomic);
+                or_add(acc + 2 * ncell + idx, (dL + dLn) * n[1], atomic);
+                or_add(acc + 3 * ncell + idx, (dL + dLn) * n[2], atomic);
             }
             if (segs) {
                 or_seg g = {idx, dsp, dtau, chiH * dsp, ray->L};
@@ -337,10 +347,16 @@ static int or_walk(const or_problem* P, const double u[3], or_ray* ray, int lmax
             if (ds < OR_NEAR) *near = 1;
             ray->L -= dL;
             ray->tau += dtau;
+            ray->Ln -= dLn;
+            ray->taun += dtaun;
             T->crossings += 1;
             T->absorbed += dL;
-            if (fabs(ray->tau - P->tau_max) < 1e-4 * P->tau_max) *near = 1;
-            if (ray->tau > P->tau_max) return OR_END_DROP;
+            T->absorbed_n += dLn;
+            /* the packet is used up once every bin it carries is: with two bins the
+             * dust-only depth (never larger than the ionizing one) decides */
+            const double tau_end = P->two_bin ? ray->taun : ray->tau;
+            if (fabs(tau_end - P->tau_max) < 1e-4 * P->tau_max) *near = 1;
+            if (tau_end > P->tau_max) return OR_END_DROP;
         }
         if (rend <= tmin) {
             if (tmin - rend < OR_NEAR) *near = 1;
@@ -383,12 +399,13 @@ static void or_trace_tree(const or_problem* P, const double u[3], int lmax, int 
         if (near) T->near_tie_rays += 1;
         if (end == OR_END_SPLIT) {
             for (int k = 3; k >= 0; --k) {
-                or_ray ch = {ray.level + 1, 4 * ray.pix + (uint64_t)k, 0.25 * ray.L, ray.tau};
+                or_ray ch = {ray.level + 1, 4 * ray.pix + (uint64_t)k, 0.25 * ray.L, ray.tau,
+                             0.25 * ray.Ln, ray.taun};
                 stack[top++] = ch;
             }
         } else {
-            if (end == OR_END_EXIT) T->escaped += ray.L;
-            else T->dropped += ray.L;
+            if (end == OR_END_EXIT) { T->escaped += ray.L; T->escaped_n += ray.Ln; }
+            else { T->dropped += ray.L; T->dropped_n += ray.Ln; }
             T->destroy += (long long)1 << (2 * (lmax_glob - ray.level));
         }
     }
@@ -407,6 +424,7 @@ static int or_setup(or_problem* P, int nx, int ny, int nz, double dx, const floa
     P->level0 = level0; P->level_cap = level_cap;
     P->m_ray = m_ray; P->tau_max = tau_max;
     P->use_rot = rot != NULL;
+    P->two_bin = 0;
     for (int i = 0; i < 9; ++i) P->rot[i] = rot ? rot[i] : (i % 4 == 0 ? 1.0 : 0.0);
     P->rmax_unit = sqrt(3.0 / (M_PI * m_ray));
     return 0;
@@ -425,13 +443,16 @@ static int or_source_cells(const or_problem* P, int nsrc, const double* lo, cons
 
 /*
  * Full multi-source trace. acc: 4*ncell doubles (G, Fx, Fy, Fz blocks), overwritten.
- * dstat[4] = {L_in, absorbed, escaped, dropped};
+ * Ln: per-source non-ionizing luminosity (a second bin, attenuated by n_H sigma_d), or NULL
+ * for one bin. dstat[8] = {L_in, absorbed, escaped, dropped} of the ionizing bin, then the
+ * same four of the non-ionizing bin.
  * istat[8 + OR_NLEVELS] = {crossings, rays, near_tie_rays, destroy, destroy_expected,
  *                          level_reached, lmax_global, 0, per_level[0..19]}.
  * Returns 0, or -1 on invalid input.
  */
 int or_trace(int nx, int ny, int nz, const double* lo, double dx, const float* nH0,
-             const float* nH, int nsrc, const double* pos, const double* L, int level0,
+             const float* nH, int nsrc, const double* pos, const double* L, const double* Ln,
+             int level0,
              int level_cap, double m_ray, double tau_max, double sigma_H, double sigma_d,
              const double* rot, double* acc, double* dstat, long long* istat, int nthreads)
 {
@@ -440,10 +461,13 @@ int or_trace(int nx, int ny, int nz, const double* lo, double dx, const float* n
                  sigma_d, rot))
         return -1;
     if (nsrc < 0) return -1;
+    P.two_bin = Ln != NULL;
     double* u = (double*)malloc(sizeof(double) * 3 * (size_t)(nsrc > 0 ? nsrc : 1));
     if (or_source_cells(&P, nsrc, lo, pos, u)) { free(u); return -1; }
     const int64_t ncell = (int64_t)nx * ny * nz;
     memset(acc, 0, sizeof(double) * 4 * (size_t)ncell);
+    double Ln_in = 0.0;
+    for (int s = 0; s < nsrc && Ln; ++s) Ln_in += Ln[s];
     int lmax_glob = level0;
     double Lin = 0.0;
     for (int s = 0; s < nsrc; ++s) {
@@ -477,7 +501,8 @@ int or_trace(int nx, int ny, int nz, const double* lo, double dx, const float* n
             int s = (int)(w / nbase);
             uint64_t p = (uint64_t)(w % nbase);
             int lm = or_level_max(&P, u + 3 * s);
-            or_ray root = {level0, p, L[s] / (double)nbase, 0.0};
+            or_ray root = {level0, p, L[s] / (double)nbase, 0.0,
+                           Ln ? Ln[s] / (double)nbase : 0.0, 0.0};
             or_trace_tree(&P, u + 3 * s, lm, lmax_glob, root, myacc, ncell, atomic, &T);
         }
 #pragma omp critical
@@ -495,6 +520,9 @@ int or_trace(int nx, int ny, int nz, const double* lo, double dx, const float* n
             tot.absorbed += T.absorbed;
             tot.escaped += T.escaped;
             tot.dropped += T.dropped;
+            tot.absorbed_n += T.absorbed_n;
+            tot.escaped_n += T.escaped_n;
+            tot.dropped_n += T.dropped_n;
         }
     }
     if (nsrc == 0) tot.level_reached = 0;
@@ -502,6 +530,10 @@ int or_trace(int nx, int ny, int nz, const double* lo, double dx, const float* n
     dstat[1] = tot.absorbed;
     dstat[2] = tot.escaped;
     dstat[3] = tot.dropped;
+    dstat[4] = Ln_in;
+    dstat[5] = tot.absorbed_n;
+    dstat[6] = tot.escaped_n;
+    dstat[7] = tot.dropped_n;
     istat[0] = tot.crossings;
     istat[1] = tot.rays;
     istat[2] = tot.near_tie_rays;
@@ -534,7 +566,7 @@ int or_ray_segments(int nx, int ny, int nz, const double* lo, double dx, const f
     if (or_source_cells(&P, 1, lo, pos, u)) return -1;
     int lm = or_level_max(&P, u);
     if (level < level0 || level > lm) return -1;
-    or_ray ray = {level, (uint64_t)pix, L, tau};
+    or_ray ray = {level, (uint64_t)pix, L, tau, 0.0, 0.0};
     or_segvec sv = {NULL, 0, 0};
     or_tally T;
     memset(&T, 0, sizeof(T));
@@ -575,7 +607,7 @@ static double or_adjoint_tree(const or_problem* P, const double u[3], int lmax, 
     double sub = 0.0;
     if (reason == OR_END_SPLIT) {
         for (int k = 0; k < 4; ++k) {
-            or_ray ch = {ray.level + 1, 4 * ray.pix + (uint64_t)k, 0.25 * end.L, end.tau};
+            or_ray ch = {ray.level + 1, 4 * ray.pix + (uint64_t)k, 0.25 * end.L, end.tau, 0.0, 0.0};
             sub += or_adjoint_tree(P, u, lmax, ch, w, K, grad);
         }
     }
@@ -633,7 +665,7 @@ int or_trace_adjoint(int nx, int ny, int nz, const double* lo, double dx, const 
             if (nt > 1) g = (double*)calloc((size_t)ncell, sizeof(double));
 #pragma omp for schedule(dynamic, 8)
             for (long long p = 0; p < nbase; ++p) {
-                or_ray root = {level0, (uint64_t)p, L[s] / (double)nbase, 0.0};
+                or_ray root = {level0, (uint64_t)p, L[s] / (double)nbase, 0.0, 0.0, 0.0};
                 ls += or_adjoint_tree(&P, u + 3 * s, lm, root, w, K, g);
             }
 #pragma omp critical

@@ -47,8 +47,8 @@ def _load():
         lib.or_pix2vec.restype = None
         lib.or_vec2pix.argtypes = [i, dp]
         lib.or_vec2pix.restype = ctypes.c_uint64
-        lib.or_trace.argtypes = [i, i, i, dp, d, fp, fp, i, dp, dp, i, i, d, d, d, d, dp, dp,
-                                 dp, lp, i]
+        lib.or_trace.argtypes = [i, i, i, dp, d, fp, fp, i, dp, dp, dp, i, i, d, d, d, d, dp,
+                                 dp, dp, lp, i]
         lib.or_trace.restype = i
         lib.or_ray_segments.argtypes = [i, i, i, dp, d, fp, fp, dp, i, i, d, d, d, d, dp, i,
                                         ctypes.c_ulonglong, d, d, lp, dp, i, P(ctypes.c_int)]
@@ -81,6 +81,7 @@ class Problem:
     m_ray: float = 4.0
     tau_max: float = 30.0
     rot: np.ndarray | None = None
+    Ln: np.ndarray | None = None          # non-ionizing luminosities: a second, dust-only bin
 
     def _args(self):
         nz, ny, nx = self.nH0.shape
@@ -88,6 +89,8 @@ class Problem:
         self._nH = None if self.nH is None else np.ascontiguousarray(self.nH, dtype=np.float32)
         self._pos = np.ascontiguousarray(np.asarray(self.pos, dtype=np.float64).reshape(-1, 3))
         self._L = np.ascontiguousarray(np.asarray(self.L, dtype=np.float64).reshape(-1))
+        self._Ln = None if self.Ln is None else np.ascontiguousarray(
+            np.asarray(self.Ln, dtype=np.float64).reshape(-1))
         self._lo = np.ascontiguousarray(np.asarray(self.lo, dtype=np.float64))
         self._rot = None if self.rot is None else np.ascontiguousarray(
             np.asarray(self.rot, dtype=np.float64).reshape(9))
@@ -106,6 +109,10 @@ class TraceResult:
     rays: int
     near_tie_rays: int
     destroy: int
+    Ln_in: float
+    absorbed_n: float
+    escaped_n: float
+    dropped_n: float
     destroy_expected: int
     level_reached: int
     level_max: int
@@ -134,12 +141,13 @@ def trace(prob: Problem, nthreads: int = 1) -> TraceResult:
     nx, ny, nz = prob._args()
     ncell = nx * ny * nz
     acc = np.zeros(4 * ncell, dtype=np.float64)
-    dstat = np.zeros(4, dtype=np.float64)
+    dstat = np.zeros(8, dtype=np.float64)
     istat = np.zeros(8 + NLEVELS, dtype=np.int64)
     rc = lib.or_trace(nx, ny, nz, _ptr(prob._lo, ctypes.c_double), prob.dx,
                       _ptr(prob._nH0, ctypes.c_float), _ptr(prob._nH, ctypes.c_float),
                       len(prob._L), _ptr(prob._pos, ctypes.c_double),
-                      _ptr(prob._L, ctypes.c_double), prob.level0, prob.level_cap,
+                      _ptr(prob._L, ctypes.c_double), _ptr(prob._Ln, ctypes.c_double),
+                      prob.level0, prob.level_cap,
                       prob.m_ray, prob.tau_max, prob.sigma_H, prob.sigma_d,
                       _ptr(prob._rot, ctypes.c_double), _ptr(acc, ctypes.c_double),
                       _ptr(dstat, ctypes.c_double), _ptr(istat, ctypes.c_longlong), nthreads)
@@ -149,6 +157,8 @@ def trace(prob: Problem, nthreads: int = 1) -> TraceResult:
     return TraceResult(G=acc[0], F=acc[1:4], L_in=dstat[0], absorbed=dstat[1],
                        escaped=dstat[2], dropped=dstat[3], crossings=int(istat[0]),
                        rays=int(istat[1]), near_tie_rays=int(istat[2]), destroy=int(istat[3]),
+                       Ln_in=dstat[4], absorbed_n=dstat[5], escaped_n=dstat[6],
+                       dropped_n=dstat[7],
                        destroy_expected=int(istat[4]), level_reached=int(istat[5]),
                        level_max=int(istat[6]), rays_per_level=istat[8:].copy(),
                        dV=prob.dx**3, sigma_H=prob.sigma_H)

@@ -195,3 +195,56 @@ def test_vacuum_inverse_square_accuracy():
     r16 = O.trace(_prob(n, pos=[[0.5, 0.5, 0.5]], level0=4, m_ray=16.0), nthreads=4)
     err16 = np.abs(r16.energy[sel] / exact - 1)
     assert np.median(err16) < 0.5 * np.median(err4)
+
+
+def test_two_bin_closed_forms():
+    """A second, non-ionizing bin (Sec. 2.3: chi_n = n_H sigma_d) on the same rays: its
+    absorption follows the exact exit lengths, and the force sums both bins' momentum
+    (Eq. e:radforce)."""
+    n = 8
+    rng = np.random.default_rng(12)
+    u = rng.uniform(1.0, 7.0, 3)
+    nH = np.full((n, n, n), 2.0)
+    nH0 = np.full((n, n, n), 0.5)
+    sH, sd = 3.0, 1.5          # chi_i = 0.5*3 + 2*1.5 = 4.5, chi_n = 3 (per unit length)
+    prob = _prob(n, nH0=nH0, pos=[u / n], L=[2.0], level0=1, level_cap=1, sigma_H=sH,
+                 sigma_d=sd, nH=nH)
+    prob.Ln = np.array([5.0])
+    r = O.trace(prob)
+    chi_i, chi_n = 0.5 * sH + 2.0 * sd, 2.0 * sd
+    want_i = want_n = 0.0
+    mom = np.zeros(3)
+    for p in range(48):
+        v = O.pix2vec(1, p)
+        s = _exit_length(u, v, n) / n
+        ai = 2.0 / 48 * (1 - math.exp(-chi_i * s))
+        an = 5.0 / 48 * (1 - math.exp(-chi_n * s))
+        want_i += ai
+        want_n += an
+        mom += (ai + an) * v
+    assert r.absorbed == pytest.approx(want_i, rel=1e-12)
+    assert r.absorbed_n == pytest.approx(want_n, rel=1e-12)
+    assert r.absorbed_n + r.escaped_n + r.dropped_n == pytest.approx(5.0, rel=1e-13)
+    assert r.Ln_in == 5.0
+    np.testing.assert_allclose(r.F.reshape(3, -1).sum(axis=1), mom, rtol=1e-12, atol=1e-15)
+    # the ionizing bin and Gamma do not see the second bin
+    one = O.trace(_prob(n, nH0=nH0, pos=[u / n], L=[2.0], level0=1, level_cap=1, sigma_H=sH,
+                        sigma_d=sd, nH=nH))
+    np.testing.assert_array_equal(r.G, one.G)
+
+
+def test_two_bin_drop_uses_the_dust_depth():
+    n = 24
+    nH = np.ones((n, n, n))
+    prob = _prob(n, nH0=nH, pos=[[0.41, 0.52, 0.47]], L=[1.0], level0=2, sigma_H=40.0,
+                 sigma_d=4.0, nH=nH, tau_max=3.0)
+    one = O.trace(prob)
+    prob.Ln = np.array([1.0])
+    two = O.trace(prob)
+    # per cell length: tau_i = 44/24 ~ 1.8, tau_n = 4/24: the ionizing bin alone is dropped
+    # within two cells; with a second bin the rays run until the dust depth passes 3
+    assert 0 < one.dropped <= math.exp(-3.0) * one.L_in
+    assert two.crossings > 5 * one.crossings
+    assert two.dropped <= math.exp(-3.0 * 44.0 / 4.0) * two.L_in
+    assert two.absorbed + two.escaped + two.dropped == pytest.approx(1.0, rel=1e-12)
+    assert two.absorbed_n + two.escaped_n + two.dropped_n == pytest.approx(1.0, rel=1e-12)
