@@ -88,6 +88,8 @@ typedef struct {
     int level_max;                                /* l_max over all sources */
     int status;                                   /* device-side status of the trace */
     int pad;
+    /* the non-ionizing bin of a two-bin trace (zero otherwise) */
+    double Ln_in, Ln_absorbed, Ln_escaped, Ln_dropped;
 } art_stats;
 
 /* Fills p with the paper's defaults: l0 = 4, m_ray = 4, tau_max = 7, sigma_H = 1,
@@ -115,7 +117,18 @@ int art_update_fields(art_grid* g, const float* d_nH0, const float* d_nH);
  * non-finite luminosity). */
 int art_add_sources(art_grid* g, int n, const double* h_pos, const double* h_L);
 
-/* Removes all sources. */
+/* Gives every source currently held a second, non-ionizing luminosity (Sec. 2.3): the trace
+ * then carries two frequency bins on each ray -- the ionizing one, attenuated by
+ * chi_i = n_H0 sigma_H + n_H sigma_d, and a non-ionizing one attenuated by dust alone,
+ * chi_n = n_H sigma_d (requires the total-density field d_nH for any attenuation) -- and the
+ * force output sums the momentum of both (Eq. e:radforce); gamma and energy stay those of
+ * the ionizing bin. A packet is retired once its dust-only optical depth (never larger than
+ * the ionizing one) exceeds tau_max. h_Ln: host, art_num_sources doubles >= 0, copied;
+ * sources added later get 0. NULL switches the second bin off. art_trace_backward covers
+ * one-bin traces only (ART_EINVAL with a second bin). Errors: ART_EINVAL, ART_ESTATE. */
+int art_set_nonionizing(art_grid* g, const double* h_Ln);
+
+/* Removes all sources (and their non-ionizing luminosities). */
 int art_clear_sources(art_grid* g);
 
 /* Number of sources currently held. */

@@ -26,7 +26,7 @@ ART_F_ROTATE = 1
 
 EXPORTED = [
     "art_params_default", "art_create_grid", "art_update_fields", "art_add_sources",
-    "art_clear_sources", "art_num_sources", "art_trace", "art_get_stats", "art_trace_backward",
+    "art_set_nonionizing", "art_clear_sources", "art_num_sources", "art_trace", "art_get_stats", "art_trace_backward",
     "art_xn_update", "art_dt_substep", "art_dt_scratch_bytes", "art_dt_substep_static",
     "art_destroy_grid", "art_strerror",
 ]
@@ -67,6 +67,10 @@ class ArtStats(ctypes.Structure):
         ("level_max", ctypes.c_int),
         ("status", ctypes.c_int),
         ("pad", ctypes.c_int),
+        ("Ln_in", ctypes.c_double),
+        ("Ln_absorbed", ctypes.c_double),
+        ("Ln_escaped", ctypes.c_double),
+        ("Ln_dropped", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -102,6 +106,8 @@ def lib():
         L.art_update_fields.restype = i
         L.art_add_sources.argtypes = [vp, i, P(d), P(d)]
         L.art_add_sources.restype = i
+        L.art_set_nonionizing.argtypes = [vp, P(d)]
+        L.art_set_nonionizing.restype = i
         L.art_clear_sources.argtypes = [vp]
         L.art_clear_sources.restype = i
         L.art_num_sources.argtypes = [vp]

@@ -122,6 +122,17 @@ class Grid:
                                         L.ctypes.data_as(P)), "art_add_sources")
         self.nsrc += len(L)
 
+    def set_nonionizing(self, Ln):
+        """Second, non-ionizing frequency bin per source (dust-attenuated); None removes it."""
+        if Ln is None:
+            C.check(C.lib().art_set_nonionizing(self._h, None), "art_set_nonionizing")
+            return
+        Ln = np.ascontiguousarray(np.asarray(Ln, dtype=np.float64).reshape(-1))
+        if len(Ln) != self.nsrc:
+            raise ValueError("one non-ionizing luminosity per source")
+        C.check(C.lib().art_set_nonionizing(self._h, Ln.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                "art_set_nonionizing")
+
     def clear_sources(self):
         C.check(C.lib().art_clear_sources(self._h), "art_clear_sources")
         self.nsrc = 0

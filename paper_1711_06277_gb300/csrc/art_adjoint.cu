@@ -218,7 +218,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
 
 __global__ void __launch_bounds__(256, 4) k_backward_persistent(const __grid_constant__ TraceArgs A)
 {
-    Tally T = {0.0, 0.0, 0ull, 0ull};
+    Tally T = {0.0, 0.0, 0ull, 0ull, 0.0, 0.0};
     DLacc D = {{0.f, 0.f}, 0xffffffffu};
     Sched* sc = A.sched;
     __shared__ int s_level, s_kind;
@@ -319,6 +319,7 @@ extern "C" int art_trace_backward(art_grid* g, const art_params* p, const float*
     p = &pp;
     const int ns = (int)g->L.size();
     if (ns == 0) return ART_ESTATE;
+    if (g->two_bin) return ART_EINVAL;  // the reverse sweep covers one-bin traces
     cudaStream_t st = g->stream;
     if ((rc = status_of(cudaMemsetAsync(g->d_stats, 0, sizeof(DevStats), st)))) return rc;
     if (!g->d_chiH && (rc = status_of(cudaMalloc((void**)&g->d_chiH, sizeof(float) * g->ncell))))

@@ -140,7 +140,8 @@ int prepare_trace(art_grid* g, const art_params* p, bool adjoint)
     const bool same = g->prep_valid && g->prep_version == g->src_version &&
                       g->prep_level0 == l0 && g->prep_level_max == p->level_max &&
                       g->prep_m_ray == p->m_ray && g->prep_adjoint == adjoint &&
-                      g->prep_schedule == p->schedule && g->prep_qcap == p->queue_capacity;
+                      g->prep_schedule == p->schedule && g->prep_qcap == p->queue_capacity &&
+                      g->prep_two_bin == g->two_bin;
     if (!same) {
         g->h_src_stage.assign(hs.data(), hs.data() + hs.size());
         if (!g->h_src_stage.data()) return ART_ENOMEM;
@@ -148,6 +149,29 @@ int prepare_trace(art_grid* g, const art_params* p, bool adjoint)
                                 cudaMemcpyHostToDevice, g->stream));
     }
     g->lmax_glob = lmax_glob;
+    if (g->two_bin && !adjoint) {
+        if ((size_t)ns > g->srcLn_cap) {
+            dev_free(g->d_srcLn);
+            g->d_srcLn = nullptr;
+            g->srcLn_cap = 0;
+            int rc = dev_alloc(&g->d_srcLn, ns);
+            if (rc) return rc;
+            g->srcLn_cap = ns;
+            g->prep_valid = false;
+        }
+        if (!same || !g->prep_valid) {
+            g->h_Ln_stage.resize(ns);
+            for (int s = 0; s < ns; ++s) g->h_Ln_stage[s] = (float)(g->Ln[s] / (double)npix0);
+            g->h_srcLn_pin.assign(g->h_Ln_stage.data(), g->h_Ln_stage.data() + ns);
+            if (!g->h_srcLn_pin.data()) return ART_ENOMEM;
+            ART_TRY(cudaMemcpyAsync(g->d_srcLn, g->h_srcLn_pin.data(), ns * sizeof(float),
+                                    cudaMemcpyHostToDevice, g->stream));
+        }
+        if (!g->d_chi2) {
+            int rc = dev_alloc(&g->d_chi2, g->ncell);
+            if (rc) return rc;
+        }
+    }
     // --- direction tables (FP64 HEALPix, rotated), rebuilt when the rotation changes
     const bool rotate = (p->flags & ART_F_ROTATE) != 0;
     bool same_rot = g->dir_rotate == rotate;
@@ -204,9 +228,11 @@ int prepare_trace(art_grid* g, const art_params* p, bool adjoint)
         else need = std::min<unsigned long long>((unsigned long long)qcap, (unsigned long long)ns * front);
         need = (need + 3) & ~3ull;
         const bool want_adj = adjoint && !g->buf_adj[l];
-        if (need > g->buf_cap[l] || want_adj) {
+        const bool want_2bin = g->two_bin && !adjoint && !g->buf_2bin[l];
+        if (need > g->buf_cap[l] || want_adj || want_2bin) {
             RayBuf& b = g->buf[l];
             dev_free(b.src); dev_free(b.pix); dev_free(b.L); dev_free(b.tau);
+            dev_free(b.Ln); dev_free(b.taun);
             dev_free(b.parent); dev_free(b.own); dev_free(b.sub);
             b = RayBuf{};
             g->buf_cap[l] = 0;
@@ -220,6 +246,11 @@ int prepare_trace(art_grid* g, const art_params* p, bool adjoint)
                 if (!rc) rc = dev_alloc(&b.own, cap);
                 if (!rc) rc = dev_alloc(&b.sub, cap);
                 g->buf_adj[l] = true;
+            }
+            if (!rc && ((g->two_bin && !adjoint) || g->buf_2bin[l])) {
+                rc = dev_alloc(&b.Ln, cap);
+                if (!rc) rc = dev_alloc(&b.taun, cap);
+                g->buf_2bin[l] = true;
             }
             if (rc) return rc;
             g->buf_cap[l] = cap;
@@ -240,12 +271,15 @@ int prepare_trace(art_grid* g, const art_params* p, bool adjoint)
     g->prep_adjoint = adjoint;
     g->prep_schedule = p->schedule;
     g->prep_qcap = p->queue_capacity;
+    g->prep_two_bin = g->two_bin;
     // --- opacity per cell length
     const double sH_dx = p->sigma_H * g->dx;
     const double sd_dx = g->nH ? p->sigma_d * g->dx : 0.0;
     int blocks = (int)std::min<long long>((g->ncell + 255) / 256, (long long)g->sms * 16);
     k_opacity<<<blocks, 256, 0, g->stream>>>(g->ncell, g->nH0, g->nH, sH_dx, sd_dx, g->d_chi,
-                                             adjoint ? g->d_chiH : nullptr, g->d_stats);
+                                             adjoint ? g->d_chiH : nullptr,
+                                             (g->two_bin && !adjoint) ? g->d_chi2 : nullptr,
+                                             g->d_stats);
     ART_TRY(cudaGetLastError());
     return ART_OK;
 }
@@ -263,6 +297,8 @@ TraceArgs make_args(art_grid* g, const art_params* p)
     A.tau_max = (float)p->tau_max;
     A.chi = g->d_chi;
     A.chiH = g->d_chiH;
+    A.chi2 = g->d_chi2;
+    A.srcLn = g->d_srcLn;
     A.acc = g->d_acc;
     A.src = g->d_src;
     A.levels = g->d_levels;
@@ -290,6 +326,12 @@ int finish_stats(art_grid* g, art_stats* out)
     out->L_dropped = d.dropped;
     out->level_reached = d.level_reached;
     out->level_max = g->last_lmax;
+    if (g->last_two_bin) {
+        out->Ln_in = g->last_Ln_in;
+        out->Ln_escaped = d.escaped_n;
+        out->Ln_dropped = d.dropped_n;
+        out->Ln_absorbed = g->last_Ln_in - d.escaped_n - d.dropped_n;
+    }
     int st = ART_OK;
     if (d.error == -1) st = ART_EINVAL;
     else if (d.error < 0) st = d.error;
@@ -378,6 +420,7 @@ int art_add_sources(art_grid* g, int n, const double* h_pos, const double* h_L)
     }
     g->pos.insert(g->pos.end(), h_pos, h_pos + 3 * (size_t)n);
     g->L.insert(g->L.end(), h_L, h_L + (size_t)n);
+    if (g->two_bin) g->Ln.insert(g->Ln.end(), (size_t)n, 0.0);
     g->src_version += 1;
     return ART_OK;
 }
@@ -387,6 +430,26 @@ int art_clear_sources(art_grid* g)
     if (!g) return ART_EINVAL;
     g->pos.clear();
     g->L.clear();
+    g->Ln.clear();
+    g->two_bin = false;
+    g->src_version += 1;
+    return ART_OK;
+}
+
+int art_set_nonionizing(art_grid* g, const double* h_Ln)
+{
+    if (!g) return ART_EINVAL;
+    if (!h_Ln) {
+        g->two_bin = false;
+        g->Ln.clear();
+        g->src_version += 1;
+        return ART_OK;
+    }
+    if (g->L.empty()) return ART_ESTATE;
+    for (size_t s = 0; s < g->L.size(); ++s)
+        if (!(h_Ln[s] >= 0.0) || !std::isfinite(h_Ln[s])) return ART_EINVAL;
+    g->Ln.assign(h_Ln, h_Ln + g->L.size());
+    g->two_bin = true;
     g->src_version += 1;
     return ART_OK;
 }
@@ -412,7 +475,8 @@ int art_trace(art_grid* g, const art_params* p, float* d_gamma, float* d_force, 
     TraceArgs A = make_args(g, p);
     if (p->schedule == ART_SCHED_PLAIN) {
         int per_sm = 0;
-        ART_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_level, threads, 0));
+        auto kern = g->two_bin ? k_trace_level<float2> : k_trace_level<float>;
+        ART_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
         if (per_sm < 1) return ART_EINVAL;
         const int grid = per_sm * g->sms;
         for (int s = 0; s < ns; ++s) {
@@ -420,7 +484,7 @@ int art_trace(art_grid* g, const art_params* p, float* d_gamma, float* d_force, 
             k_inject<<<(npix0 + 255) / 256, 256, 0, g->stream>>>(s, 1, npix0, g->buf[l0],
                                                                   &g->d_sched->count[l0]);
             for (int l = l0; l <= g->src_lmax[s]; ++l)
-                k_trace_level<<<grid, threads, 0, g->stream>>>(A, l);
+                kern<<<grid, threads, 0, g->stream>>>(A, l);
         }
         ART_TRY(cudaGetLastError());
     } else {
@@ -429,7 +493,8 @@ int art_trace(art_grid* g, const art_params* p, float* d_gamma, float* d_force, 
                                                                      &g->d_sched->count[l0]);
         ART_TRY(cudaGetLastError());
         int per_sm = 0;
-        ART_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent, threads, 0));
+        auto kern = g->two_bin ? k_trace_persistent<float2> : k_trace_persistent<float>;
+        ART_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
         if (per_sm < 1) return ART_EINVAL;
         if (p->blocks_per_sm > 0 && p->blocks_per_sm < per_sm) per_sm = p->blocks_per_sm;
         cudaLaunchConfig_t cfg;
@@ -442,7 +507,7 @@ int art_trace(art_grid* g, const art_params* p, float* d_gamma, float* d_force, 
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        ART_TRY(cudaLaunchKernelEx(&cfg, k_trace_persistent, A));
+        ART_TRY(cudaLaunchKernelEx(&cfg, kern, A));
     }
     const double dV = g->dx * g->dx * g->dx;
     const float gscale = (float)(p->sigma_H * g->dx / dV);
@@ -457,6 +522,9 @@ int art_trace(art_grid* g, const art_params* p, float* d_gamma, float* d_force, 
     double Lin = 0.0;
     for (double v : g->L) Lin += v;
     g->last_L_in = Lin;
+    g->last_two_bin = g->two_bin;
+    g->last_Ln_in = 0.0;
+    for (double v : g->Ln) g->last_Ln_in += v;
     g->last_lmax = g->lmax_glob;
     g->destroy_expected = (unsigned long long)ns * (12ull << (2 * g->lmax_glob));
     g->last_kind = 0;
@@ -485,11 +553,14 @@ void art_destroy_grid(art_grid* g)
     dev_free(g->d_stats);
     dev_free(g->d_srcL);
     dev_free(g->d_rec);
+    dev_free(g->d_chi2);
+    dev_free(g->d_srcLn);
     dev_free(g->d_dL_scratch);
     for (int l = 0; l < kNL; ++l) {
         dev_free(g->dir[l]);
         RayBuf& b = g->buf[l];
         dev_free(b.src); dev_free(b.pix); dev_free(b.L); dev_free(b.tau);
+        dev_free(b.Ln); dev_free(b.taun);
         dev_free(b.parent); dev_free(b.own); dev_free(b.sub);
     }
     if (g->h_stats) cudaFreeHost(g->h_stats);

@@ -98,6 +98,8 @@ struct RayBuf {
     unsigned* pix;
     float* L;
     float* tau;
+    float* Ln;          // two-bin traces: entering L and tau of the non-ionizing bin
+    float* taun;
     // adjoint extras (NULL in forward traces)
     unsigned* parent;   // slot of the parent in the level above
     float2* own;        // weighted sum over the ray's own segments (pass 1), double-float
@@ -109,6 +111,7 @@ struct RayBuf {
 struct Tally {
     double escaped, dropped;
     unsigned long long crossings, destroy;
+    double escaped_n, dropped_n;  // non-ionizing bin of two-bin traces
 };
 
 // Device-resident counters of one trace.
@@ -116,6 +119,7 @@ struct DevStats {
     unsigned long long crossings, destroy, rays_total;
     unsigned long long rays_per_level[kNL];
     double escaped, dropped;
+    double escaped_n, dropped_n;
     int level_reached;
     int error;
 };
@@ -138,6 +142,8 @@ struct TraceArgs {
     int chunk;
     float tau_max;
     const float* chi;        // opacity per cell times dx (per cell length)
+    const float2* chi2;      // two-bin traces: {chi_i, chi_n} per cell length
+    const float* srcLn;      // two-bin traces: base-ray non-ionizing luminosity per source
     const float* chiH;       // neutral-H part of chi (adjoint only)
     const float4* rec;       // adjoint: per cell {chi, chi_H, w, 0}
     const float* w;          // adjoint weights per cell
@@ -163,11 +169,17 @@ enum : int { EV_NONE = 0, EV_EXIT = 1, EV_DROP = 2, EV_SPLIT = 3 };
 // {opacity, its neutral-H part, loss weight, unused} (adjoint).
 __device__ __forceinline__ float chi_of(const float& c) { return c; }
 __device__ __forceinline__ float chi_of(const float4& c) { return c.x; }
+__device__ __forceinline__ float chi_of(const float2& c) { return c.x; }
+// A cell record of two floats marks a two-bin trace: {chi_i, chi_n}.
+template <class Cell> struct TwoBin { static constexpr bool value = false; };
+template <> struct TwoBin<float2> { static constexpr bool value = true; };
 __device__ __forceinline__ float load_cell(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float4 load_cell(const float4* p) { return __ldg(p); }
+__device__ __forceinline__ float2 load_cell(const float2* p) { return __ldg(p); }
 template <class Cell> __device__ __forceinline__ Cell cell_zero();
 template <> __device__ __forceinline__ float cell_zero<float>() { return 0.f; }
 template <> __device__ __forceinline__ float4 cell_zero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+template <> __device__ __forceinline__ float2 cell_zero<float2>() { return make_float2(0.f, 0.f); }
 
 template <class Cell>
 struct WalkT {
@@ -178,6 +190,7 @@ struct WalkT {
     int rem[3];   // cells left on each axis before the ray leaves the grid
     float n[3];   // direction (hi parts) for momentum deposits
     float L, tau;
+    float Ln, taun;  // non-ionizing bin (two-bin traces only)
     Cell cell;    // record of the current cell (prefetched)
 };
 using Walk = WalkT<float>;
@@ -227,6 +240,7 @@ struct StepOut {
     float G;      // L_in ds phi(dtau)
     float dL;     // L_in (1 - e^-dtau)
     float phi;    // (1 - e^-dtau)/dtau
+    float dLn;    // two-bin traces: loss of the non-ionizing bin (chi_n = n_H sigma_d)
     int ev;
 };
 
@@ -329,7 +343,19 @@ __device__ __forceinline__ StepOut walk_step(WalkT<Cell>& W, bool splits, df rma
         o.dL = 0.f;
     }
     W.tau += x;
-    const bool drop = seg && W.tau > tau_max;
+    bool drop;
+    if constexpr (TwoBin<Cell>::value) {
+        // second bin on the same ray; the packet is used up once its dust-only depth (never
+        // the larger one) passes tau_max
+        const float xn = W.cell.y * ds;
+        o.dLn = W.Ln * xn * phi_of(xn);
+        W.Ln = W.Ln - o.dLn;
+        W.taun += xn;
+        drop = seg && W.taun > tau_max;
+    } else {
+        o.dLn = 0.f;
+        drop = seg && W.tau > tau_max;
+    }
     o.ev = drop ? EV_DROP : (split ? EV_SPLIT : (out ? EV_EXIT : EV_NONE));
     // advance: the earliest axis by select, further tied axes on the side path
     const df dsel = df_sel(a == 0, W.d[0], df_sel(a == 1, W.d[1], W.d[2]));
@@ -396,27 +422,32 @@ __device__ __forceinline__ void deposit(float4* __restrict__ acc, int cell, floa
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ void tally_flush(const Tally& T, DevStats* st)
 {
-    __shared__ double s_d[2];
+    __shared__ double s_d[4];
     __shared__ unsigned long long s_u[2];
-    if (threadIdx.x == 0) { s_d[0] = s_d[1] = 0.0; s_u[0] = s_u[1] = 0ull; }
+    if (threadIdx.x == 0) { s_d[0] = s_d[1] = s_d[2] = s_d[3] = 0.0; s_u[0] = s_u[1] = 0ull; }
     __syncthreads();
-    double e = T.escaped, d = T.dropped;
+    double e = T.escaped, d = T.dropped, en = T.escaped_n, dn = T.dropped_n;
     unsigned long long c = T.crossings, w = T.destroy;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         e += __shfl_down_sync(kFull, e, off);
         d += __shfl_down_sync(kFull, d, off);
+        en += __shfl_down_sync(kFull, en, off);
+        dn += __shfl_down_sync(kFull, dn, off);
         c += __shfl_down_sync(kFull, c, off);
         w += __shfl_down_sync(kFull, w, off);
     }
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&s_d[0], e); atomicAdd(&s_d[1], d);
+        atomicAdd(&s_d[2], en); atomicAdd(&s_d[3], dn);
         atomicAdd(&s_u[0], c); atomicAdd(&s_u[1], w);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         atomicAdd(&st->escaped, s_d[0]);
         atomicAdd(&st->dropped, s_d[1]);
+        if (s_d[2] != 0.0) atomicAdd(&st->escaped_n, s_d[2]);
+        if (s_d[3] != 0.0) atomicAdd(&st->dropped_n, s_d[3]);
         atomicAdd(&st->crossings, s_u[0]);
         atomicAdd(&st->destroy, s_u[1]);
     }
@@ -452,6 +483,10 @@ __device__ __forceinline__ int ray_begin(const TraceArgs& A, const LevelInfo& LV
     const bool inside = walk_start(W, A.nx, A.ny, A.nz, u, n, inv, LV.r0);
     W.L = L0;
     W.tau = tau0;
+    if constexpr (TwoBin<Cell>::value) {
+        W.Ln = (l == A.level0) ? __ldg(A.srcLn + s) : __ldcg(B.Ln + i);
+        W.taun = (l == A.level0) ? 0.f : __ldcg(B.taun + i);
+    }
     W.cell = inside ? __ldg(cells + W.idx) : cell_zero<Cell>();
     return inside ? 1 : 0;
 }

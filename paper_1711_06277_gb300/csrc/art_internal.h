@@ -41,6 +41,14 @@ struct art_grid {
     const float* nH0 = nullptr;  // borrowed
     const float* nH = nullptr;   // borrowed, may be NULL
     std::vector<double> pos, L;  // host copies of the sources
+    std::vector<double> Ln;      // non-ionizing luminosities (two-bin traces)
+    bool two_bin = false;
+    float2* d_chi2 = nullptr;    // {chi_i, chi_n} per cell length (two-bin traces)
+    float* d_srcLn = nullptr;    // base-ray non-ionizing luminosity per source
+    size_t srcLn_cap = 0;
+    std::vector<float> h_Ln_stage;
+    PinnedVec<float> h_srcLn_pin;
+    bool buf_2bin[art::kNL] = {};
     std::vector<int> src_lmax;
 
     // device buffers owned by the grid
@@ -76,7 +84,7 @@ struct art_grid {
     PinnedVec<art::SrcDev> h_src_stage;          // pinned staging of the source table
     unsigned long long src_version = 0;
     unsigned long long prep_version = 0;
-    bool prep_valid = false, prep_adjoint = false;
+    bool prep_valid = false, prep_adjoint = false, prep_two_bin = false;
     int prep_level0 = -1, prep_level_max = -2, prep_schedule = -1;
     double prep_m_ray = 0.0;
     long long prep_qcap = -1;
@@ -85,6 +93,8 @@ struct art_grid {
     int last_lmax = 0;
     int last_kind = 0;  // 0 forward, 1 backward
     double last_L_in = 0.0;
+    double last_Ln_in = 0.0;
+    bool last_two_bin = false;
     unsigned long long destroy_expected = 0;
     bool traced = false;
 };

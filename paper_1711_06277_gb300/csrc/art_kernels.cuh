@@ -113,7 +113,7 @@ __global__ void k_directions(int level, unsigned long long npix, double r0, doub
 __global__ void k_opacity(long long ncell, const float* __restrict__ nH0,
                           const float* __restrict__ nH, double sH_dx, double sd_dx,
                           float* __restrict__ chi, float* __restrict__ chiH,
-                          DevStats* __restrict__ st)
+                          float2* __restrict__ chi2, DevStats* __restrict__ st)
 {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     long long step = (long long)gridDim.x * blockDim.x;
@@ -123,8 +123,10 @@ __global__ void k_opacity(long long ncell, const float* __restrict__ nH0,
         float b = nH ? nH[i] : 0.f;
         bad = bad || !(a >= 0.f) || !(b >= 0.f) || isinf(a) || isinf(b);
         double h = (double)a * sH_dx;
-        chi[i] = __double2float_rn(h + (double)b * sd_dx);
+        const double dust = (double)b * sd_dx;
+        chi[i] = __double2float_rn(h + dust);
         if (chiH) chiH[i] = __double2float_rn(h);
+        if (chi2) chi2[i] = make_float2(__double2float_rn(h + dust), __double2float_rn(dust));
     }
     if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicCAS(&st->error, 0, -1);
 }
@@ -150,9 +152,17 @@ __global__ void k_inject(int s0, int nsrc, unsigned npix0, RayBuf B, unsigned lo
 // the pixel order of this one; parents that do not split mark their four slots empty. Idle
 // lanes are refilled once at least a quarter of the warp is idle, so the ray set-up runs
 // with many lanes at once. Warp-uniform: every lane of the warp must call it.
-__device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
-                         unsigned long long begin, unsigned long long end, Tally& T)
+// The per-cell records a trace gathers: opacities (one bin) or opacity pairs (two bins).
+template <class Cell> __device__ __forceinline__ const Cell* cells_of(const TraceArgs& A);
+template <> __device__ __forceinline__ const float* cells_of<float>(const TraceArgs& A) { return A.chi; }
+template <> __device__ __forceinline__ const float2* cells_of<float2>(const TraceArgs& A) { return A.chi2; }
+
+template <class Cell>
+__device__ void run_rays(const TraceArgs& A, const Cell* cells, int l,
+                         unsigned long long* cursor, unsigned long long begin,
+                         unsigned long long end, Tally& T)
 {
+    constexpr bool two = TwoBin<Cell>::value;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt = (1u << lane) - 1u;
     const LevelInfo LV = A.levels[l];
@@ -166,7 +176,7 @@ __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
     unsigned wnext = 0, wend = 0;
     bool more = true;
     bool active = false;
-    Walk W;
+    WalkT<Cell> W;
     unsigned s = 0, p = 0;
     unsigned slot = 0;
     float L0 = 0.f;
@@ -192,7 +202,7 @@ __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
                 const unsigned rank = __popc(need & lt);
                 if (!active && rank < avail) {
                     slot = wnext + rank;
-                    const int st = ray_begin(A, LV, B, l, slot, W, A.chi, s, p, L0, splits);
+                    const int st = ray_begin(A, LV, B, l, slot, W, cells, s, p, L0, splits);
                     if (st > 0) {
                         active = true;
                         first = base;
@@ -200,6 +210,7 @@ __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
                     } else {
                         if (st == 0) {  // starts outside the grid: escapes with its full L
                             T.escaped += (double)L0;
+                            if constexpr (two) T.escaped_n += (double)W.Ln;
                             T.destroy += LV.destroy_w;
                             ++nrays;
                         }
@@ -220,10 +231,11 @@ __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
             int cell = -1;
             float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
             if (active) {
-                const StepOut o = walk_step<false>(W, splits, LV.rmax, sy, sz, A.chi, A.tau_max);
+                const StepOut o = walk_step<false>(W, splits, LV.rmax, sy, sz, cells, A.tau_max);
                 if (o.cell >= 0) {
                     cell = o.cell;
-                    dv = make_float4(o.G, o.dL * W.n[0], o.dL * W.n[1], o.dL * W.n[2]);
+                    const float dm = two ? o.dL + o.dLn : o.dL;  // momentum of both bins
+                    dv = make_float4(o.G, dm * W.n[0], dm * W.n[1], dm * W.n[2]);
                     ++ncross;
                 }
                 if (o.ev != EV_NONE) {
@@ -238,12 +250,22 @@ __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
                             *reinterpret_cast<float4*>(C.L + c4) = make_float4(Lc, Lc, Lc, Lc);
                             *reinterpret_cast<float4*>(C.tau + c4) =
                                 make_float4(W.tau, W.tau, W.tau, W.tau);
+                            if constexpr (two) {
+                                const float Ln = 0.25f * W.Ln;
+                                *reinterpret_cast<float4*>(C.Ln + c4) = make_float4(Ln, Ln, Ln, Ln);
+                                *reinterpret_cast<float4*>(C.taun + c4) =
+                                    make_float4(W.taun, W.taun, W.taun, W.taun);
+                            }
                         } else {
                             atomicCAS(&A.stats->error, 0, -3);  // ART_EQUEUE_OVERFLOW
                         }
                     } else {
                         if (o.ev == EV_EXIT) T.escaped += (double)W.L;
                         else T.dropped += (double)W.L;
+                        if constexpr (two) {
+                            if (o.ev == EV_EXIT) T.escaped_n += (double)W.Ln;
+                            else T.dropped_n += (double)W.Ln;
+                        }
                         T.destroy += LV.destroy_w;
                         if (has_next) write_holes(C, c4);
                     }
@@ -259,14 +281,15 @@ __device__ void run_rays(const TraceArgs& A, int l, unsigned long long* cursor,
 }
 
 // Plain schedule: all slots of level l (one source's front).
+template <class Cell>
 __global__ void __launch_bounds__(512, 2) k_trace_level(const __grid_constant__ TraceArgs A, int l)
 {
-    Tally T = {0.0, 0.0, 0ull, 0ull};
+    Tally T = {0.0, 0.0, 0ull, 0ull, 0.0, 0.0};
     // a front that overflowed (status set by the writer) is cut at the buffer capacity
     const unsigned long long end =
         min(*((volatile unsigned long long*)&A.sched->count[l]), A.buf[l].cap);
     if (blockIdx.x == 0 && threadIdx.x == 0 && l < A.lmax_glob) A.sched->count[l + 1] = 4 * end;
-    run_rays(A, l, &A.sched->cursor[l], 0, end, T);
+    run_rays(A, cells_of<Cell>(A), l, &A.sched->cursor[l], 0, end, T);
     tally_flush(T, A.stats);
 }
 
@@ -278,9 +301,10 @@ __global__ void k_reset_counts(Sched* sc)
 }
 
 // Persistent schedule: all sources, all levels, one cooperative launch.
+template <class Cell>
 __global__ void __launch_bounds__(512, 2) k_trace_persistent(const __grid_constant__ TraceArgs A)
 {
-    Tally T = {0.0, 0.0, 0ull, 0ull};
+    Tally T = {0.0, 0.0, 0ull, 0ull, 0.0, 0.0};
     Sched* sc = A.sched;
     __shared__ int s_level;
     __shared__ unsigned long long s_begin, s_end;
@@ -316,7 +340,7 @@ __global__ void __launch_bounds__(512, 2) k_trace_persistent(const __grid_consta
         __syncthreads();
         const int l = s_level;
         if (l < 0) break;
-        run_rays(A, l, &sc->cursor[l], s_begin, s_end, T);
+        run_rays(A, cells_of<Cell>(A), l, &sc->cursor[l], s_begin, s_end, T);
     }
     tally_flush(T, A.stats);
 }

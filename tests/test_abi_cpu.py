@@ -23,7 +23,7 @@ def _declared():
 def test_exports_every_declared_symbol():
     lib = C.lib()
     names = _declared()
-    assert len(names) >= 14
+    assert len(names) >= 16
     for n in names:
         assert hasattr(lib, n), n
     assert sorted(C.EXPORTED) == names

@@ -180,3 +180,60 @@ def test_integer_tallies_deterministic(art):
     for k in ("crossings", "rays_total", "rays_per_level", "destroy"):
         assert a["stats"][k] == b["stats"][k]
     np.testing.assert_allclose(a["gamma"], b["gamma"], rtol=1e-5, atol=1e-6 * a["gamma"].max())
+
+
+@pytest.mark.parametrize("schedule", ["persistent", "plain"])
+def test_two_bin_dust_radiation_pressure(art, schedule):
+    """Second, non-ionizing bin (Sec. 2.3): dust-only attenuation, force of both bins."""
+    n = 48
+    rho = synth.lognormal_field(n, 1.5, seed=11)
+    pos = synth.uniform_positions(4, seed=11)
+    L = synth.power_law_luminosities(4, seed=11)
+    Ln = 3.0 * synth.power_law_luminosities(4, seed=12)
+    nH0, nH = 0.3 * rho, rho
+    p = art.Params(level0=3, tau_max=30.0, sigma_H=20.0, sigma_d=6.0, schedule=schedule)
+    dev = torch.device("cuda")
+    g = art.Grid(torch.as_tensor(nH0.astype(np.float32), device=dev), 1.0 / n,
+                 nH=torch.as_tensor(nH.astype(np.float32), device=dev))
+    g.add_sources(pos, L)
+    g.set_nonionizing(Ln)
+    out = g.trace(p, force=True, energy=True)
+    res = {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in out.items()}
+    prob = O.Problem(nH0=nH0, pos=pos, L=L, dx=1.0 / n, nH=nH, sigma_H=20.0, sigma_d=6.0,
+                     level0=3, tau_max=30.0, Ln=Ln)
+    ref = O.trace(prob, nthreads=8)
+    st = res["stats"]
+    assert st["status"] == 0 and st["destroy"] == st["destroy_expected"]
+    PA.compare_field(res["gamma"], ref.gamma, what="gamma")
+    chi = nH0.astype(np.float32).astype(np.float64) * 20.0 + nH.astype(np.float32).astype(np.float64) * 6.0
+    chin = nH.astype(np.float32).astype(np.float64) * 6.0
+    # bound of the two-bin force: chi_i E_i + the non-ionizing absorption in the cell
+    Fn_bound = np.abs(ref.force).sum(axis=0) + chi * ref.energy
+    PA.compare_force(res["force"], ref.force, np.maximum(Fn_bound, chi * ref.energy))
+    if ref.near_tie_rays == 0:
+        assert st["crossings"] == ref.crossings
+    assert abs(st["Ln_escaped"] - ref.escaped_n) <= PA.CONS * ref.Ln_in
+    assert abs(st["Ln_dropped"] - ref.dropped_n) <= PA.CONS * ref.Ln_in
+    assert st["Ln_in"] == pytest.approx(ref.Ln_in, rel=1e-12)
+    g.close()
+
+
+def test_two_bin_matches_one_bin_without_second_luminosity(art):
+    n = 32
+    rho = synth.lognormal_field(n, 1.0, seed=13).astype(np.float32)
+    pos = synth.uniform_positions(2, seed=13)
+    p = art.Params(level0=2, tau_max=30.0, sigma_H=8.0, sigma_d=1.0)
+    dev = torch.device("cuda")
+    g = art.Grid(torch.as_tensor(rho, device=dev), 1.0 / n, nH=torch.as_tensor(rho, device=dev))
+    g.add_sources(pos, [1.0, 0.5])
+    one = g.trace(p, force=True)
+    g.set_nonionizing([0.0, 0.0])
+    two = g.trace(p, force=True)
+    # with tau_max far above the dust depth both retire rays at the same places (exit)
+    torch.testing.assert_close(one["gamma"], two["gamma"], rtol=0, atol=0)
+    torch.testing.assert_close(one["force"], two["force"], rtol=0, atol=0)
+    from paper_1711_06277_gb300 import _lib as C
+    with pytest.raises(C.ArtError) as e:
+        g.trace_backward(p, torch.ones_like(one["gamma"]))
+    assert e.value.status == C.ART_EINVAL
+    g.close()
