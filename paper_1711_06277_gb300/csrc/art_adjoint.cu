@@ -124,8 +124,8 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
                         ++nrays;
                     } else {  // no ray, or no segment at all: a finished leaf with zero sums
                         if (st == 0) {
-                            T.escaped += (double)L0;
-                            T.destroy += LV.destroy_w;
+                            atomicAdd(&T.escaped, (double)L0);
+                            atomicAdd(&T.destroy, LV.destroy_w);
                             ++nrays;
                         }
                         B.own[slot] = nan2;
@@ -192,9 +192,9 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
                             }
                             mode = 0;
                         } else {
-                            if (o.ev == EV_EXIT) T.escaped += (double)W.L;
-                            else T.dropped += (double)W.L;
-                            T.destroy += LV.destroy_w;
+                            if (o.ev == EV_EXIT) atomicAdd(&T.escaped, (double)W.L);
+                            else atomicAdd(&T.dropped, (double)W.L);
+                            atomicAdd(&T.destroy, LV.destroy_w);
                             if (has_next) write_holes(C, c4);
                             B.own[slot] = nan2;  // finished within this phase
                             total = own.hi + own.lo;
@@ -212,13 +212,14 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
             if (cell >= 0) atomicAdd(A.grad + cell, val);
         }
     }
-    T.crossings += ncross;
+    tally_crossings(T, ncross);
     count_rays(A.stats, l, nrays);
 }
 
 __global__ void __launch_bounds__(256, 4) k_backward_persistent(const __grid_constant__ TraceArgs A)
 {
-    Tally T = {0.0, 0.0, 0ull, 0ull, 0.0, 0.0};
+    tally_init();
+    Tally& T = tally_slots()[threadIdx.x >> 5];
     DLacc D = {{0.f, 0.f}, 0xffffffffu};
     Sched* sc = A.sched;
     __shared__ int s_level, s_kind;
@@ -273,7 +274,7 @@ __global__ void __launch_bounds__(256, 4) k_backward_persistent(const __grid_con
         run_adjoint(A, l, s_kind, &sc->cursor[l], s_begin, s_end, T, D);
     }
     if (D.src != 0xffffffffu && D.v.hi != 0.f) atomicAdd(A.dL + D.src, (double)D.v.hi + (double)D.v.lo);
-    tally_flush(T, A.stats);
+    tally_flush(A.stats);
 }
 
 // Per-cell record of the reverse sweep: one 16-byte gather per crossing.

@@ -420,36 +420,49 @@ __device__ __forceinline__ void deposit(float4* __restrict__ acc, int cell, floa
 // ---------------------------------------------------------------------------------------
 // helpers shared by the forward and backward kernels
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ void tally_flush(const Tally& T, DevStats* st)
+// Per-warp tallies live in shared memory (one Tally per warp, updated with shared atomics
+// when a ray ends), so they cost no registers in the walk loop.
+__device__ __forceinline__ Tally* tally_slots()
 {
-    __shared__ double s_d[4];
-    __shared__ unsigned long long s_u[2];
-    if (threadIdx.x == 0) { s_d[0] = s_d[1] = s_d[2] = s_d[3] = 0.0; s_u[0] = s_u[1] = 0ull; }
+    __shared__ Tally s_t[32];
+    return s_t;
+}
+
+__device__ __forceinline__ void tally_init()
+{
+    Tally* t = tally_slots();
+    if (threadIdx.x < 32) t[threadIdx.x] = Tally{0.0, 0.0, 0ull, 0ull, 0.0, 0.0};
     __syncthreads();
-    double e = T.escaped, d = T.dropped, en = T.escaped_n, dn = T.dropped_n;
-    unsigned long long c = T.crossings, w = T.destroy;
+}
+
+// Adds a lane count of crossings to its warp's tally.
+__device__ __forceinline__ void tally_crossings(Tally& T, unsigned n)
+{
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        e += __shfl_down_sync(kFull, e, off);
-        d += __shfl_down_sync(kFull, d, off);
-        en += __shfl_down_sync(kFull, en, off);
-        dn += __shfl_down_sync(kFull, dn, off);
-        c += __shfl_down_sync(kFull, c, off);
-        w += __shfl_down_sync(kFull, w, off);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&s_d[0], e); atomicAdd(&s_d[1], d);
-        atomicAdd(&s_d[2], en); atomicAdd(&s_d[3], dn);
-        atomicAdd(&s_u[0], c); atomicAdd(&s_u[1], w);
-    }
+    for (int off = 16; off > 0; off >>= 1) n += __shfl_down_sync(kFull, n, off);
+    if ((threadIdx.x & 31u) == 0 && n > 0) atomicAdd(&T.crossings, (unsigned long long)n);
+}
+
+__device__ __forceinline__ void tally_flush(DevStats* st)
+{
     __syncthreads();
     if (threadIdx.x == 0) {
-        atomicAdd(&st->escaped, s_d[0]);
-        atomicAdd(&st->dropped, s_d[1]);
-        if (s_d[2] != 0.0) atomicAdd(&st->escaped_n, s_d[2]);
-        if (s_d[3] != 0.0) atomicAdd(&st->dropped_n, s_d[3]);
-        atomicAdd(&st->crossings, s_u[0]);
-        atomicAdd(&st->destroy, s_u[1]);
+        const Tally* t = tally_slots();
+        Tally s = {0.0, 0.0, 0ull, 0ull, 0.0, 0.0};
+        for (int w = 0; w < (int)((blockDim.x + 31) / 32); ++w) {
+            s.escaped += t[w].escaped;
+            s.dropped += t[w].dropped;
+            s.escaped_n += t[w].escaped_n;
+            s.dropped_n += t[w].dropped_n;
+            s.crossings += t[w].crossings;
+            s.destroy += t[w].destroy;
+        }
+        atomicAdd(&st->escaped, s.escaped);
+        atomicAdd(&st->dropped, s.dropped);
+        if (s.escaped_n != 0.0) atomicAdd(&st->escaped_n, s.escaped_n);
+        if (s.dropped_n != 0.0) atomicAdd(&st->dropped_n, s.dropped_n);
+        atomicAdd(&st->crossings, s.crossings);
+        atomicAdd(&st->destroy, s.destroy);
     }
 }
 

@@ -229,9 +229,11 @@ def test_two_bin_matches_one_bin_without_second_luminosity(art):
     one = g.trace(p, force=True)
     g.set_nonionizing([0.0, 0.0])
     two = g.trace(p, force=True)
-    # with tau_max far above the dust depth both retire rays at the same places (exit)
-    torch.testing.assert_close(one["gamma"], two["gamma"], rtol=0, atol=0)
-    torch.testing.assert_close(one["force"], two["force"], rtol=0, atol=0)
+    # with tau_max far above the dust depth both retire rays at the same places (exit); the
+    # sums differ only by FP32 summation order
+    assert one["stats"]["crossings"] == two["stats"]["crossings"]
+    torch.testing.assert_close(one["gamma"], two["gamma"], rtol=1e-5, atol=1e-6 * float(one["gamma"].max()))
+    torch.testing.assert_close(one["force"], two["force"], rtol=1e-5, atol=1e-6 * float(one["force"].abs().max()))
     from paper_1711_06277_gb300 import _lib as C
     with pytest.raises(C.ArtError) as e:
         g.trace_backward(p, torch.ones_like(one["gamma"]))
