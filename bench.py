@@ -426,7 +426,8 @@ def main():
                           + (", trace + Eq. e:xn3 update per step" if cfg["alpha"] else ""),
               "grid": cfg["n"], "sources": cfg["nsrc"], "schedule": args.schedule,
               "cuda_graph": args.graph,
-              "l2": "inputs larger than L2 (512 MB density, 2 GB accumulator)"}
+              "l2": (f"inputs larger than L2 ({cfg['n'] ** 3 * 4 >> 20} MB density, "
+                     f"{cfg['n'] ** 3 * 16 >> 20} MB accumulator; L2 is 129 MB)")}
 
     if args.impl == "reference":
         if rank != 0:

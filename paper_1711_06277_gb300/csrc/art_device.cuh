@@ -290,7 +290,11 @@ __device__ __forceinline__ StepOut walk_step(WalkT<Cell>& W, bool splits, df rma
     df tm = df_sel(a == 0, W.t[0], df_sel(a == 1, W.t[1], W.t[2]));
     bool split = splits && rmax.hi < hm;
     bool m0 = a == 0, m1 = a == 1, m2 = a == 2;
-    bool single = true;
+    // next cell and whether it leaves the grid, for the usual single-axis crossing
+    const float na = a == 0 ? W.n[0] : (a == 1 ? W.n[1] : W.n[2]);
+    const int st = a == 0 ? 1 : (a == 1 ? sy : sz);
+    int nidx = W.idx + (na > 0.f ? st : -st);
+    bool out = (a == 0 ? W.rem[0] : (a == 1 ? W.rem[1] : W.rem[2])) == 0;
     if (h0 == h1 || h0 == h2 || h1 == h2 || (splits && rmax.hi == hm)) {
         const bool e01 = df_le(W.t[0], W.t[1]);
         tm = df_sel(e01, W.t[0], W.t[1]);
@@ -305,23 +309,15 @@ __device__ __forceinline__ StepOut walk_step(WalkT<Cell>& W, bool splits, df rma
         m0 = df_diff(W.t[0], tm) <= tol;
         m1 = df_diff(W.t[1], tm) <= tol;
         m2 = df_diff(W.t[2], tm) <= tol;
-        single = (int)m0 + (int)m1 + (int)m2 == 1;
+        nidx = W.idx + (m0 ? (W.n[0] > 0.f ? 1 : -1) : 0) + (m1 ? (W.n[1] > 0.f ? sy : -sy) : 0) +
+               (m2 ? (W.n[2] > 0.f ? sz : -sz) : 0);
+        out = (m0 && W.rem[0] == 0) || (m1 && W.rem[1] == 0) || (m2 && W.rem[2] == 0);
+        // tied axes other than a advance here; axis a advances with the common path below
+        if (m0 && a != 0) W.t[0] = df_add(W.t[0], W.d[0]);
+        if (m1 && a != 1) W.t[1] = df_add(W.t[1], W.d[1]);
+        if (m2 && a != 2) W.t[2] = df_add(W.t[2], W.d[2]);
     }
     o.ds = df_diff(split ? rmax : tm, W.tc);
-    // next cell and whether it leaves the grid
-    int nidx = W.idx;
-    bool out;
-    if (single) {
-        const float na = a == 0 ? W.n[0] : (a == 1 ? W.n[1] : W.n[2]);
-        const int st = a == 0 ? 1 : (a == 1 ? sy : sz);
-        const int r = a == 0 ? W.rem[0] : (a == 1 ? W.rem[1] : W.rem[2]);
-        nidx += na > 0.f ? st : -st;
-        out = r == 0;
-    } else {
-        nidx += (m0 ? (W.n[0] > 0.f ? 1 : -1) : 0) + (m1 ? (W.n[1] > 0.f ? sy : -sy) : 0) +
-                (m2 ? (W.n[2] > 0.f ? sz : -sz) : 0);
-        out = (m0 && W.rem[0] == 0) || (m1 && W.rem[1] == 0) || (m2 && W.rem[2] == 0);
-    }
     const bool go = !split && !out;
     const Cell ncell = go ? load_cell(cells + nidx) : cell_zero<Cell>();  // prefetch
     // deposit in the current cell (segments of length <= 0 deposit nothing)
@@ -366,11 +362,6 @@ __device__ __forceinline__ StepOut walk_step(WalkT<Cell>& W, bool splits, df rma
     W.rem[0] -= m0 ? 1 : 0;
     W.rem[1] -= m1 ? 1 : 0;
     W.rem[2] -= m2 ? 1 : 0;
-    if (!single) {
-        if (m0 && a != 0) W.t[0] = df_add(W.t[0], W.d[0]);
-        if (m1 && a != 1) W.t[1] = df_add(W.t[1], W.d[1]);
-        if (m2 && a != 2) W.t[2] = df_add(W.t[2], W.d[2]);
-    }
     W.tc = tm;
     W.idx = nidx;
     W.cell = ncell;

@@ -232,12 +232,10 @@ __device__ void run_rays(const TraceArgs& A, const Cell* cells, int l,
             float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
             if (active) {
                 const StepOut o = walk_step<false>(W, splits, LV.rmax, sy, sz, cells, A.tau_max);
-                if (o.cell >= 0) {
-                    cell = o.cell;
-                    const float dm = two ? o.dL + o.dLn : o.dL;  // momentum of both bins
-                    dv = make_float4(o.G, dm * W.n[0], dm * W.n[1], dm * W.n[2]);
-                    ++ncross;
-                }
+                cell = o.cell;  // < 0 when the segment had no length
+                const float dm = two ? o.dL + o.dLn : o.dL;  // momentum of both bins
+                dv = make_float4(o.G, dm * W.n[0], dm * W.n[1], dm * W.n[2]);
+                ncross += o.cell >= 0 ? 1u : 0u;
                 if (o.ev != EV_NONE) {
                     active = false;
                     const unsigned long long c4 = 4ull * (slot - b32);

@@ -222,15 +222,15 @@ def test_two_bin_matches_one_bin_without_second_luminosity(art):
     n = 32
     rho = synth.lognormal_field(n, 1.0, seed=13).astype(np.float32)
     pos = synth.uniform_positions(2, seed=13)
-    p = art.Params(level0=2, tau_max=30.0, sigma_H=8.0, sigma_d=1.0)
+    # tau_max beyond any ray's depth: both traces retire rays only at the grid boundary
+    p = art.Params(level0=2, tau_max=1e4, sigma_H=8.0, sigma_d=1.0)
     dev = torch.device("cuda")
     g = art.Grid(torch.as_tensor(rho, device=dev), 1.0 / n, nH=torch.as_tensor(rho, device=dev))
     g.add_sources(pos, [1.0, 0.5])
     one = g.trace(p, force=True)
     g.set_nonionizing([0.0, 0.0])
     two = g.trace(p, force=True)
-    # with tau_max far above the dust depth both retire rays at the same places (exit); the
-    # sums differ only by FP32 summation order
+    # the sums differ only by FP32 summation order
     assert one["stats"]["crossings"] == two["stats"]["crossings"]
     torch.testing.assert_close(one["gamma"], two["gamma"], rtol=1e-5, atol=1e-6 * float(one["gamma"].max()))
     torch.testing.assert_close(one["force"], two["force"], rtol=1e-5, atol=1e-6 * float(one["force"].abs().max()))
