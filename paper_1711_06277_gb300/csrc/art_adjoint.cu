@@ -31,7 +31,6 @@ using namespace art;
 
 namespace {
 
-enum : int { PH_EXPAND = 0, PH_COLLAPSE = 1 };
 
 // d/dx of (1 - e^-x)/x. Taylor series below 1 (no cancellation), closed form above.
 __device__ __forceinline__ float dphi_of(float x, float em)
@@ -70,8 +69,21 @@ __device__ __forceinline__ void dl_add(DLacc& D, double* dL, unsigned s, df own)
     D.v = df_add(D.v, own);
 }
 
-// One phase of the reverse sweep on rays [cursor .. end) of level l. Warp-uniform.
-__device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long long* cursor,
+__device__ __forceinline__ void red_f32(float* p, float v)
+{
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+
+// One expand phase of the reverse sweep on the rays in slots [cursor .. end) of level l
+// (phase starting at slot `begin`). Pass 1 walks each ray for its own weighted sum. A ray
+// that splits stores that sum, a pending-children count of 4 and its children (in order, as
+// in the forward trace). A ray that ends walks again at once (pass 2) and deposits its
+// gradients; it then adds its total to its parent and counts the parent down. The lane that
+// brings a parent's count to zero takes over the parent's pass 2 (its level below this
+// phase's), and so on towards the base level: no separate collapse phase is needed, because
+// the deepest-first schedule does not reuse a level's slots before everything below it has
+// finished. Warp-uniform.
+__device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* cursor,
                             unsigned long long begin, unsigned long long end, Tally& T, DLacc& D)
 {
     const unsigned lane = threadIdx.x & 31u;
@@ -79,17 +91,16 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
     const LevelInfo LV = A.levels[l];
     const RayBuf B = A.buf[l];
     const RayBuf C = A.buf[l + 1];
-    const RayBuf P = l > A.level0 ? A.buf[l - 1] : A.buf[l];
     const bool has_next = l < A.lmax_glob;
     const float gs = A.gscale;
     const int sy = A.nx, sz = A.nx * A.ny;
-    const float2 nan2 = make_float2(__int_as_float(0x7fc00000), 0.f);
 
     // slot indices fit in 32 bits (level buffers hold fewer than 2^31 slots)
     const unsigned b32 = (unsigned)begin, e32 = (unsigned)end;
     unsigned wnext = 0, wend = 0;
     bool more = true;
-    int mode = 0;  // 0 idle, 1 pass 1, 2 pass 2
+    int mode = 0;          // 0 idle, 1 pass 1 (level l), 2 pass 2 (level lv <= l)
+    int lv = l;            // level of the ray being walked
     WalkT<float4> W;
     unsigned s = 0, p = 0;
     unsigned slot = 0;
@@ -97,77 +108,100 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
     df own = {0.f, 0.f};   // own weighted sum (pass 1), kept for dL in pass 2
     float total = 0.f;     // own + descendants (pass 2), passed to the parent
     df rem = {0.f, 0.f};   // weighted sum over what follows the current segment (pass 2)
+    df rmax = LV.rmax;     // split radius of level lv
     bool splits = false;
     unsigned ncross = 0, nrays = 0;
 
+    // Completion of the ray in `slot` at level lv (pass 2 done, or a ray without segments):
+    // dL, the parent's sum, and possibly the parent's pass 2 in this lane.
+    auto complete = [&]() {
+        for (;;) {
+            dl_add(D, A.dL, __ldcg(A.buf[lv].src + slot), own);
+            if (lv == A.level0) { mode = 0; return; }
+            const RayBuf Bl = A.buf[lv];
+            const RayBuf Pl = A.buf[lv - 1];
+            const unsigned par = __ldcg(Bl.parent + slot);
+            if (total != 0.f) red_f32(Pl.sub + par, total);
+            __threadfence();
+            if (atomicSub(Pl.pending + par, 1u) != 1u) { mode = 0; return; }
+            // last child: this lane replays the parent (pass 2)
+            __threadfence();
+            lv -= 1;
+            slot = par;
+            const float2 ov = __ldcg(Pl.own + slot);
+            own = {ov.x, ov.y};
+            rem = df_add(own, {__ldcg(Pl.sub + slot), 0.f});
+            total = rem.hi + rem.lo;
+            const LevelInfo Lp = A.levels[lv];
+            rmax = Lp.rmax;
+            ray_begin(A, Lp, Pl, lv, slot, W, A.rec, s, p, L0, splits);
+            Ls = __ldg(A.srcL + s);
+            mode = 2;
+            return;
+        }
+    };
+
     for (;;) {
         unsigned need = __ballot_sync(kFull, mode == 0);
-        while (need && more) {
-            if (wnext >= wend) {
-                unsigned long long b = 0;
-                if (lane == 0) b = atomicAdd(cursor, (unsigned long long)A.chunk);
-                b = __shfl_sync(kFull, b, 0);
-                if (b >= end) { more = false; break; }
-                wnext = (unsigned)b;
-                wend = min(wnext + (unsigned)A.chunk, e32);
-            }
-            const unsigned avail = min(wend - wnext, 32u);
-            const unsigned rank = __popc(need & lt);
-            if (mode == 0 && rank < avail) {
-                slot = wnext + rank;
-                if (kind == PH_EXPAND) {
+        if (__popc(need) >= 8 || need == kFull) {
+            while (need && more) {
+                if (wnext >= wend) {
+                    unsigned long long b = 0;
+                    if (lane == 0) b = atomicAdd(cursor, (unsigned long long)A.chunk);
+                    b = __shfl_sync(kFull, b, 0);
+                    if (b >= end) { more = false; break; }
+                    wnext = (unsigned)b;
+                    wend = min(wnext + (unsigned)A.chunk, e32);
+                }
+                const unsigned avail = min(wend - wnext, 32u);
+                const unsigned rank = __popc(need & lt);
+                if (mode == 0 && rank < avail) {
+                    slot = wnext + rank;
+                    lv = l;
+                    rmax = LV.rmax;
                     const int st = ray_begin(A, LV, B, l, slot, W, A.rec, s, p, L0, splits);
                     if (st > 0) {
                         Ls = __ldg(A.srcL + s);
                         mode = 1;
                         own = {0.f, 0.f};
                         ++nrays;
-                    } else {  // no ray, or no segment at all: a finished leaf with zero sums
-                        if (st == 0) {
+                    } else {
+                        if (has_next) write_holes(C, 4ull * (slot - b32));
+                        if (st == 0) {  // starts outside the grid: a leaf with zero sums
                             atomicAdd(&T.escaped, (double)L0);
                             atomicAdd(&T.destroy, LV.destroy_w);
                             ++nrays;
+                            own = {0.f, 0.f};
+                            total = 0.f;
+                            complete();
                         }
-                        B.own[slot] = nan2;
-                        if (has_next) write_holes(C, 4ull * (slot - b32));
-                    }
-                } else {
-                    const float2 ov = __ldcg(B.own + slot);
-                    if (ov.x == ov.x) {  // a split ray waiting for its collapse
-                        own = {ov.x, ov.y};
-                        rem = df_add(own, {__ldcg(B.sub + slot), 0.f});
-                        total = rem.hi + rem.lo;
-                        ray_begin(A, LV, B, l, slot, W, A.rec, s, p, L0, splits);
-                        Ls = __ldg(A.srcL + s);
-                        mode = 2;
                     }
                 }
+                wnext += min(avail, (unsigned)__popc(need));
+                need = __ballot_sync(kFull, mode == 0);
             }
-            wnext += min(avail, (unsigned)__popc(need));
-            need = __ballot_sync(kFull, mode == 0);
         }
-        if (!__any_sync(kFull, mode != 0)) break;
+        if (!__any_sync(kFull, mode != 0)) {
+            if (!more) break;
+            continue;
+        }
 
 #pragma unroll 1
-        for (int k = 0; k < 4; ++k) {
-            int cell = -1;
-            float val = 0.f;
+        for (int k = 0; k < 8; ++k) {
             if (mode != 0) {
                 const float wv = W.cell.z;   // weight and neutral-H opacity of this cell
                 const float hv = W.cell.y;
-                const StepOut o = walk_step<false>(W, splits, LV.rmax, sy, sz, A.rec, A.tau_max);
-                if (o.cell >= 0) {
-                    const float g = wv * gs * o.G;
-                    if (mode == 1) {
-                        own = df_add(own, {g, 0.f});
-                        ++ncross;
-                    } else {
-                        rem = df_add(rem, {-g, 0.f});
-                        const float after = rem.hi + rem.lo;
-                        const float dphi = dphi_of(o.dtau, -o.dtau * o.phi);
-                        val = Ls * hv * o.ds * (wv * gs * o.Lin * o.ds * dphi - after);
-                        cell = o.cell;
-                    }
+                const StepOut o = walk_step<false>(W, splits, rmax, sy, sz, A.rec, A.tau_max);
+                const float g = wv * gs * o.G;
+                if (mode == 1) {
+                    own = df_add(own, {g, 0.f});
+                    ncross += o.cell >= 0 ? 1u : 0u;
+                } else {
+                    rem = df_add(rem, {-g, 0.f});
+                    const float after = rem.hi + rem.lo;
+                    const float dphi = dphi_of(o.dtau, -o.dtau * o.phi);
+                    const float val = Ls * hv * o.ds * (wv * gs * o.Lin * o.ds * dphi - after);
+                    if (o.cell >= 0) red_f32(A.grad + o.cell, val);
                 }
                 if (o.ev != EV_NONE) {
                     if (mode == 1) {
@@ -175,18 +209,17 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
                         if (o.ev == EV_SPLIT) {
                             B.own[slot] = make_float2(own.hi, own.lo);
                             B.sub[slot] = 0.f;
+                            B.pending[slot] = 4u;
                             if (c4 + 4 <= C.cap) {
                                 const float Lc = 0.25f * W.L;
-                                const unsigned ps = (unsigned)slot;
-                                const unsigned rs = __ldcg(B.src + slot);  // reloaded: not kept live
-                                const unsigned rp = __ldcg(B.pix + slot);
-                                *reinterpret_cast<uint4*>(C.src + c4) = make_uint4(rs, rs, rs, rs);
+                                *reinterpret_cast<uint4*>(C.src + c4) = make_uint4(s, s, s, s);
                                 *reinterpret_cast<uint4*>(C.pix + c4) =
-                                    make_uint4(4 * rp, 4 * rp + 1, 4 * rp + 2, 4 * rp + 3);
+                                    make_uint4(4 * p, 4 * p + 1, 4 * p + 2, 4 * p + 3);
                                 *reinterpret_cast<float4*>(C.L + c4) = make_float4(Lc, Lc, Lc, Lc);
                                 *reinterpret_cast<float4*>(C.tau + c4) =
                                     make_float4(W.tau, W.tau, W.tau, W.tau);
-                                *reinterpret_cast<uint4*>(C.parent + c4) = make_uint4(ps, ps, ps, ps);
+                                *reinterpret_cast<uint4*>(C.parent + c4) =
+                                    make_uint4(slot, slot, slot, slot);
                             } else {
                                 atomicCAS(&A.stats->error, 0, -3);
                             }
@@ -196,20 +229,17 @@ __device__ void run_adjoint(const TraceArgs& A, int l, int kind, unsigned long l
                             else atomicAdd(&T.dropped, (double)W.L);
                             atomicAdd(&T.destroy, LV.destroy_w);
                             if (has_next) write_holes(C, c4);
-                            B.own[slot] = nan2;  // finished within this phase
+                            // a leaf: pass 2 right away
                             total = own.hi + own.lo;
                             rem = own;
                             ray_begin(A, LV, B, l, slot, W, A.rec, s, p, L0, splits);
                             mode = 2;
                         }
                     } else {
-                        if (l > A.level0) atomicAdd(P.sub + __ldcg(B.parent + slot), total);
-                        dl_add(D, A.dL, __ldcg(B.src + slot), own);
-                        mode = 0;
+                        complete();
                     }
                 }
             }
-            if (cell >= 0) atomicAdd(A.grad + cell, val);
         }
     }
     tally_crossings(T, ncross);
@@ -222,7 +252,7 @@ __global__ void __launch_bounds__(256, 4) k_backward_persistent(const __grid_con
     Tally& T = tally_slots()[threadIdx.x >> 5];
     DLacc D = {{0.f, 0.f}, 0xffffffffu};
     Sched* sc = A.sched;
-    __shared__ int s_level, s_kind;
+    __shared__ int s_level;
     __shared__ unsigned long long s_begin, s_end;
     for (;;) {
         if (!grid_barrier(sc, A.stats, A.wait_ns)) break;
@@ -230,33 +260,20 @@ __global__ void __launch_bounds__(256, 4) k_backward_persistent(const __grid_con
             volatile Sched* v = sc;
             int l = -1;
             for (int k = A.lmax_glob; k >= A.level0; --k)
-                if (v->count[k] > 0 || v->chunk_state[k] == 1) { l = k; break; }
+                if (v->count[k] > 0) { l = k; break; }
             if (l < 0) {
                 v->done = 1;
-            } else if (v->chunk_state[l] == 1) {
-                v->chunk_state[l] = 0;
-                v->phase_level = l;
-                v->phase_kind = PH_COLLAPSE;
-                v->phase_begin = v->chunk_begin[l];
-                v->phase_end = v->chunk_end[l];
-                v->cursor[l] = v->chunk_begin[l];
             } else {
-                unsigned long long have = min(v->count[l], A.buf[l].cap);
+                const unsigned long long have = min(v->count[l], A.buf[l].cap);
                 unsigned long long take = have;
                 if (l < A.lmax_glob) take = min(have, A.buf[l + 1].cap / 4);
                 const unsigned long long b = have - take;
                 v->count[l] = b;
                 v->phase_level = l;
-                v->phase_kind = PH_EXPAND;
                 v->phase_begin = b;
                 v->phase_end = have;
                 v->cursor[l] = b;
-                if (l < A.lmax_glob) {
-                    v->chunk_state[l] = 1;
-                    v->chunk_begin[l] = b;
-                    v->chunk_end[l] = have;
-                    v->count[l + 1] = 4 * take;  // the children's slots
-                }
+                if (l < A.lmax_glob) v->count[l + 1] = 4 * take;  // the children's slots
             }
             __threadfence();
         }
@@ -264,14 +281,13 @@ __global__ void __launch_bounds__(256, 4) k_backward_persistent(const __grid_con
         if (threadIdx.x == 0) {
             volatile Sched* v = sc;
             s_level = v->done ? -1 : v->phase_level;
-            s_kind = v->phase_kind;
             s_begin = v->phase_begin;
             s_end = v->phase_end;
         }
         __syncthreads();
         const int l = s_level;
         if (l < 0) break;
-        run_adjoint(A, l, s_kind, &sc->cursor[l], s_begin, s_end, T, D);
+        run_adjoint(A, l, &sc->cursor[l], s_begin, s_end, T, D);
     }
     if (D.src != 0xffffffffu && D.v.hi != 0.f) atomicAdd(A.dL + D.src, (double)D.v.hi + (double)D.v.lo);
     tally_flush(A.stats);

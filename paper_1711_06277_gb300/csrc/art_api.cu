@@ -233,7 +233,7 @@ int prepare_trace(art_grid* g, const art_params* p, bool adjoint)
             RayBuf& b = g->buf[l];
             dev_free(b.src); dev_free(b.pix); dev_free(b.L); dev_free(b.tau);
             dev_free(b.Ln); dev_free(b.taun);
-            dev_free(b.parent); dev_free(b.own); dev_free(b.sub);
+            dev_free(b.parent); dev_free(b.own); dev_free(b.sub); dev_free(b.pending);
             b = RayBuf{};
             g->buf_cap[l] = 0;
             const unsigned long long cap = std::max(need, g->buf_cap_req[l]);
@@ -245,6 +245,7 @@ int prepare_trace(art_grid* g, const art_params* p, bool adjoint)
                 rc = dev_alloc(&b.parent, cap);
                 if (!rc) rc = dev_alloc(&b.own, cap);
                 if (!rc) rc = dev_alloc(&b.sub, cap);
+                if (!rc) rc = dev_alloc(&b.pending, cap);
                 g->buf_adj[l] = true;
             }
             if (!rc && ((g->two_bin && !adjoint) || g->buf_2bin[l])) {
@@ -561,7 +562,7 @@ void art_destroy_grid(art_grid* g)
         RayBuf& b = g->buf[l];
         dev_free(b.src); dev_free(b.pix); dev_free(b.L); dev_free(b.tau);
         dev_free(b.Ln); dev_free(b.taun);
-        dev_free(b.parent); dev_free(b.own); dev_free(b.sub);
+        dev_free(b.parent); dev_free(b.own); dev_free(b.sub); dev_free(b.pending);
     }
     if (g->h_stats) cudaFreeHost(g->h_stats);
     if (g->h_levels) cudaFreeHost(g->h_levels);

@@ -104,6 +104,7 @@ struct RayBuf {
     unsigned* parent;   // slot of the parent in the level above
     float2* own;        // weighted sum over the ray's own segments (pass 1), double-float
     float* sub;         // weighted sum over the ray's descendants (added by the children)
+    unsigned* pending;  // children of a split ray still to finish
     unsigned long long cap;
 };
 
@@ -129,8 +130,6 @@ struct Sched {
     unsigned long long count[kNL];   // rays held in the level buffer (a stack, top = count)
     unsigned long long cursor[kNL];  // next ray of the current phase / launch
     unsigned long long phase_begin, phase_end;
-    unsigned long long chunk_begin[kNL], chunk_end[kNL];  // adjoint: expanded range per level
-    int chunk_state[kNL];
     int phase_level, phase_kind, done, pad;
     unsigned bar_count, bar_gen;
 };

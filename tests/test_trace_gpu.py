@@ -239,3 +239,41 @@ def test_two_bin_matches_one_bin_without_second_luminosity(art):
         g.trace_backward(p, torch.ones_like(one["gamma"]))
     assert e.value.status == C.ART_EINVAL
     g.close()
+
+
+def test_zero_luminosity_and_thin_slab(art):
+    """A source with L = 0 deposits nothing; a one-cell-thick slab (nz = 1) still matches."""
+    shape = (1, 40, 33)
+    rng = np.random.default_rng(5)
+    rho = rng.random(shape) * 2
+    dx = 0.05
+    pos = np.array([[0.7, 1.1, 0.025], [0.3, 0.4, 0.02]])
+    L = np.array([0.0, 1.5])
+    p = art.Params(level0=3, tau_max=30.0, sigma_H=3.0)
+    res = _run(art, rho, pos, L, dx, p)
+    ref = O.trace(O.Problem(nH0=rho, pos=pos, L=L, dx=dx, sigma_H=3.0, level0=3, tau_max=30.0),
+                  nthreads=8)
+    _check(res, ref, rho, p, exact_counts=ref.near_tie_rays == 0)
+    only0 = _run(art, rho, pos[:1], L[:1], dx, p)
+    assert np.all(only0["gamma"] == 0) and np.all(only0["force"] == 0)
+
+
+def test_sources_added_and_fields_updated_between_traces(art):
+    n = 40
+    rng = np.random.default_rng(8)
+    rho = rng.random((n, n, n)).astype(np.float32) + 0.1
+    dev = torch.device("cuda")
+    t = torch.from_numpy(rho.copy()).to(dev)
+    g = art.Grid(t, 1.0 / n)
+    p = art.Params(level0=2, tau_max=30.0, sigma_H=4.0)
+    pos = synth.uniform_positions(3, seed=8)
+    g.add_sources(pos[:2], [1.0, 2.0])
+    g.trace(p)
+    g.add_sources(pos[2:], [0.5])           # a third source after a trace
+    t.mul_(0.5)                             # fields are read again by every trace
+    out = g.trace(p, force=True, energy=True)
+    res = {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in out.items()}
+    ref = O.trace(O.Problem(nH0=0.5 * rho, pos=pos, L=[1.0, 2.0, 0.5], dx=1.0 / n, sigma_H=4.0,
+                            level0=2, tau_max=30.0), nthreads=8)
+    _check(res, ref, 0.5 * rho, p, exact_counts=ref.near_tie_rays == 0)
+    g.close()
