@@ -10,16 +10,16 @@
 // factor e^-dtau of segment j). Split points and tau_max retirement are held fixed.
 //
 // Nothing is stored per segment. Rays are traced with unit source luminosity (the loss is
-// linear in each L_s; gradients are scaled by L_s when deposited) in a reverse-level sweep of
-// the persistent schedule:
-//   expand phase (level l chunk): pass 1 replays each ray and sums its own weighted G; a
-//     split ray stores that sum and emits its children (with a back-pointer); a ray that
-//     ends there replays again at once (pass 2) and deposits its gradients;
-//   collapse phase (the same chunk, once every descendant is finished): each split ray
-//     replays (pass 2) with S = own + children's sums, depositing its gradients, and adds its
-//     total to its parent.
-// The phase order is deepest-first, as in the forward schedule, so children always finish
-// before their parents' collapse and every level buffer stays bounded.
+// linear in each L_s; gradients are scaled by L_s when deposited) in the deepest-first phases
+// of the persistent schedule, and every ray is walked twice:
+//   pass 1 sums the ray's own weighted G; a ray that splits stores that sum, a count of 4
+//     pending children and its children (with a back-pointer to it);
+//   pass 2 (S = own sum + the children's totals) deposits the gradients and adds the ray's
+//     total to its parent's. A ray that ends without splitting runs pass 2 at once; the lane
+//     whose child brings a parent's pending count to zero runs the parent's pass 2, and so on
+//     towards the base level.
+// Children always finish before their parent's pass 2 because the count only reaches zero
+// after all four of them have added their totals.
 #include <cmath>
 #include <algorithm>
 #include <cstring>
@@ -374,6 +374,7 @@ extern "C" int art_trace_backward(art_grid* g, const art_params* p, const float*
         if ((rc = status_of(cudaGetLastError()))) return rc;
     }
     TraceArgs A = make_args(g, p);
+    if (p->chunk == 0) A.chunk = 32;  // measured best for the reverse sweep (64 for the forward)
     A.rec = g->d_rec;
     A.w = d_w;
     A.grad = d_dlog_nH0;
