@@ -21,11 +21,13 @@ def art():
 
 
 def _case(A, n, nsrc, seed, sigma_ln=1.5, tau_box=10.0, level0=4, nH_scale=None,
-          schedule="persistent"):
+          schedule="persistent", signed=False):
     rho = synth.lognormal_field(n, sigma_ln, seed=seed).astype(np.float32)
     pos = synth.uniform_positions(nsrc, seed=seed)
     L = synth.power_law_luminosities(nsrc, seed=seed)
     w = synth.uniform_weights(n, seed=seed).astype(np.float32)
+    if signed:
+        w = (2.0 * w - 1.0).astype(np.float32)
     p = A.Params(level0=level0, tau_max=30.0, sigma_H=tau_box, schedule=schedule)
     nH = None if nH_scale is None else (nH_scale * rho).astype(np.float32)
     if nH is not None:
@@ -71,6 +73,18 @@ def test_adjoint_config4_128_16src(art):
 def test_adjoint_with_dust_and_deep_levels(art):
     out, ref, L = _case(art, 48, 3, seed=8, level0=1, nH_scale=1.3)
     _check(out, ref, L)
+
+
+def test_adjoint_signed_weights(art):
+    """w of both signs (a general upstream gradient): per-cell sums cancel, so the gradient
+    is compared in the max norm (1e-5 of its peak) and dL per source relatively."""
+    out, ref, L = _case(art, 64, 5, seed=11, signed=True)
+    rg, rdL, rloss = ref
+    assert out["stats"]["status"] == 0
+    err = np.abs(out["grad"].astype(np.float64) - rg).max() / np.abs(rg).max()
+    assert err <= PA.REL, f"signed-weight gradient: max-norm rel err {err:.3e}"
+    scale = np.abs(rdL).max()
+    assert np.abs(out["dL"] - rdL).max() <= PA.REL * scale
 
 
 def test_autograd_function_matches_backward(art):
