@@ -580,20 +580,23 @@ int or_ray_segments(int nx, int ny, int nz, const double* lo, double dx, const f
 }
 
 /* ------------------------------------------------------------------------------------- */
-/* Reverse sweep for loss = sum_c w_c Gamma_c (new; no counterpart in the paper)          */
+/* Reverse sweep for loss = sum_c (w_c Gamma_c + v_c . f_rad,c) (new; not in the paper)    */
 /* ------------------------------------------------------------------------------------- */
 
 /*
- * For a ray and its descendants returns S = sum of w K G over all their segments, and adds
+ * For a ray and its descendants returns S, the sum of their segments' loss terms
+ *   w_c K G + q dL,   G = L_in ds phi(dtau),  dL = L_in (1 - e^-dtau),  q = KF (v_c . n),
+ * with K = sigma_H / dV (Gamma per unit G) and KF = 1 / dV (force per unit momentum), and adds
  * to grad[c] the derivative of the loss with respect to log n_H0[c]:
- *   own term    w_c K L_in ds phi'(dtau) dtauH
+ *   own term    (w_c K L_in ds phi'(dtau) + q L_in e^-dtau) dtauH
  *   later terms -S_after dtauH,
- * where S_after is the weighted sum over every later segment of the ray and of all its
+ * where S_after is the loss over every later segment of the ray and over all of its
  * descendants (their entering luminosity carries the factor e^-dtau of this segment).
- * tau_max and the split points are held fixed.
+ * v may be NULL (no force term). tau_max and the split points are held fixed.
  */
 static double or_adjoint_tree(const or_problem* P, const double u[3], int lmax, or_ray ray,
-                              const double* w, double K, double* grad)
+                              const double* w, const double* v, int64_t ncell, double K,
+                              double KF, double* grad)
 {
     or_segvec sv = {NULL, 0, 0};
     or_tally T;
@@ -601,14 +604,23 @@ static double or_adjoint_tree(const or_problem* P, const double u[3], int lmax, 
     int near = 0;
     or_ray end = ray;
     int reason = or_walk(P, u, &end, lmax, NULL, 0, 0, &sv, &T, &near);
+    double n[3];
+    or_direction(P, ray.level, ray.pix, n);
     double own = 0.0;
-    for (size_t j = 0; j < sv.n; ++j)
-        own += w[sv.v[j].cell] * K * sv.v[j].Lin * sv.v[j].ds * or_phi(sv.v[j].dtau);
+    for (size_t j = 0; j < sv.n; ++j) {
+        const or_seg* g = &sv.v[j];
+        own += w[g->cell] * K * g->Lin * g->ds * or_phi(g->dtau);
+        if (v) {
+            const double q = KF * (v[g->cell] * n[0] + v[ncell + g->cell] * n[1] +
+                                   v[2 * ncell + g->cell] * n[2]);
+            own += q * -g->Lin * expm1(-g->dtau);
+        }
+    }
     double sub = 0.0;
     if (reason == OR_END_SPLIT) {
         for (int k = 0; k < 4; ++k) {
             or_ray ch = {ray.level + 1, 4 * ray.pix + (uint64_t)k, 0.25 * end.L, end.tau, 0.0, 0.0};
-            sub += or_adjoint_tree(P, u, lmax, ch, w, K, grad);
+            sub += or_adjoint_tree(P, u, lmax, ch, w, v, ncell, K, KF, grad);
         }
     }
     double total = own + sub;
@@ -616,23 +628,31 @@ static double or_adjoint_tree(const or_problem* P, const double u[3], int lmax, 
     for (size_t j = 0; j < sv.n; ++j) {
         const or_seg* g = &sv.v[j];
         double gj = w[g->cell] * K * g->Lin * g->ds * or_phi(g->dtau);
+        double dj = w[g->cell] * K * g->Lin * g->ds * or_dphi(g->dtau);
+        if (v) {
+            const double q = KF * (v[g->cell] * n[0] + v[ncell + g->cell] * n[1] +
+                                   v[2 * ncell + g->cell] * n[2]);
+            gj += q * -g->Lin * expm1(-g->dtau);
+            dj += q * g->Lin * exp(-g->dtau);
+        }
         after -= gj;
-        grad[g->cell] += g->dtauH * (w[g->cell] * K * g->Lin * g->ds * or_dphi(g->dtau) - after);
+        grad[g->cell] += g->dtauH * (dj - after);
     }
     free(sv.v);
     return total;
 }
 
 /*
- * Gradient of loss = sum_c w_c Gamma_c with respect to log n_H0 (per cell, into grad) and
- * to each source luminosity (dL[s] = loss_s / L_s, the loss being linear in L_s).
+ * Gradient of loss = sum_c (w_c Gamma_c + v_c . f_rad,c) with respect to log n_H0 (per cell,
+ * into grad) and to each source luminosity (dL[s] = loss_s / L_s, the loss being linear in
+ * L_s). v: 3*ncell values (x block, y block, z block) or NULL for the Gamma term alone.
  * Returns 0, or -1 on invalid input (including a source with L_s <= 0).
  */
 int or_trace_adjoint(int nx, int ny, int nz, const double* lo, double dx, const float* nH0,
                      const float* nH, int nsrc, const double* pos, const double* L, int level0,
                      int level_cap, double m_ray, double tau_max, double sigma_H, double sigma_d,
-                     const double* rot, const double* w, double* grad, double* dL,
-                     double* loss, int nthreads)
+                     const double* rot, const double* w, const double* v, double* grad,
+                     double* dL, double* loss, int nthreads)
 {
     or_problem P;
     if (or_setup(&P, nx, ny, nz, dx, nH0, nH, level0, level_cap, m_ray, tau_max, sigma_H,
@@ -645,6 +665,7 @@ int or_trace_adjoint(int nx, int ny, int nz, const double* lo, double dx, const 
     const int64_t ncell = (int64_t)nx * ny * nz;
     memset(grad, 0, sizeof(double) * (size_t)ncell);
     const double K = sigma_H / (dx * dx * dx);
+    const double KF = 1.0 / (dx * dx * dx);
     const long long nbase = 12LL << (2 * level0);
     double total = 0.0;
 #ifdef _OPENMP
@@ -666,7 +687,7 @@ int or_trace_adjoint(int nx, int ny, int nz, const double* lo, double dx, const 
 #pragma omp for schedule(dynamic, 8)
             for (long long p = 0; p < nbase; ++p) {
                 or_ray root = {level0, (uint64_t)p, L[s] / (double)nbase, 0.0, 0.0, 0.0};
-                ls += or_adjoint_tree(&P, u + 3 * s, lm, root, w, K, g);
+                ls += or_adjoint_tree(&P, u + 3 * s, lm, root, w, v, ncell, K, KF, g);
             }
 #pragma omp critical
             if (g != grad) {

@@ -54,7 +54,7 @@ def _load():
                                         ctypes.c_ulonglong, d, d, lp, dp, i, P(ctypes.c_int)]
         lib.or_ray_segments.restype = i
         lib.or_trace_adjoint.argtypes = [i, i, i, dp, d, fp, fp, i, dp, dp, i, i, d, d, d, d,
-                                         dp, dp, dp, dp, dp, i]
+                                         dp, dp, dp, dp, dp, dp, i]
         lib.or_trace_adjoint.restype = i
         _lib = lib
     return _lib
@@ -186,14 +186,20 @@ def ray_segments(prob: Problem, level: int, pix: int, L: float = 1.0, tau: float
     return cells[:n].copy(), ds[:n].copy(), end.value
 
 
-def trace_adjoint(prob: Problem, w: np.ndarray, nthreads: int = 1):
-    """d loss / d log n_H0 per cell and d loss / d L per source for loss = sum_c w_c Gamma_c."""
+def trace_adjoint(prob: Problem, w: np.ndarray, nthreads: int = 1, v: np.ndarray | None = None):
+    """d loss / d log n_H0 per cell and d loss / d L per source for
+    loss = sum_c (w_c Gamma_c + v_c . f_rad,c); v has shape (3, nz, ny, nx) or is None."""
     lib = _load()
     nx, ny, nz = prob._args()
     ncell = nx * ny * nz
     w64 = np.ascontiguousarray(np.asarray(w, dtype=np.float64).reshape(-1))
     if w64.size != ncell:
         raise ValueError("w must have one entry per cell")
+    v64 = None
+    if v is not None:
+        v64 = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(-1))
+        if v64.size != 3 * ncell:
+            raise ValueError("v must have three entries per cell")
     grad = np.zeros(ncell, dtype=np.float64)
     dL = np.zeros(len(prob._L), dtype=np.float64)
     loss = ctypes.c_double(0.0)
@@ -203,8 +209,8 @@ def trace_adjoint(prob: Problem, w: np.ndarray, nthreads: int = 1):
                               _ptr(prob._L, ctypes.c_double), prob.level0, prob.level_cap,
                               prob.m_ray, prob.tau_max, prob.sigma_H, prob.sigma_d,
                               _ptr(prob._rot, ctypes.c_double), _ptr(w64, ctypes.c_double),
-                              _ptr(grad, ctypes.c_double), _ptr(dL, ctypes.c_double),
-                              ctypes.byref(loss), nthreads)
+                              _ptr(v64, ctypes.c_double), _ptr(grad, ctypes.c_double),
+                              _ptr(dL, ctypes.c_double), ctypes.byref(loss), nthreads)
     if rc != 0:
         raise ValueError("oracle rejected the problem")
     return grad.reshape(nz, ny, nx), dL, loss.value
