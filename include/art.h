@@ -154,16 +154,20 @@ int art_trace(art_grid* g, const art_params* p, float* d_gamma, float* d_force,
  * trace). Returns the device status of that trace. ART_ESTATE if nothing was traced. */
 int art_get_stats(art_grid* g, art_stats* h_stats);
 
-/* Gradient of loss = sum_c w_c gamma_c for the fields and sources of the last call
- * (new; the paper has no adjoint): recomputes every ray's path in reverse level order
- * instead of storing segments, summing child-ray adjoints into their parents.
- *   d_w:          device, ncell floats, dloss/dgamma per cell;
+/* Gradient of loss = sum_c (w_c gamma_c + v_c . force_c) for the fields and sources of the
+ * last call (new; the paper has no adjoint): recomputes every ray's path in reverse level
+ * order instead of storing segments, summing child-ray adjoints into their parents.
+ *   d_w:          device, ncell floats, dloss/dgamma per cell, or NULL (no gamma term);
+ *   d_v:          device, 3*ncell floats (SoA blocks x, y, z, like art_trace's d_force),
+ *                 dloss/dforce per cell, or NULL (no force term); not both NULL;
  *   d_dlog_nH0:   device, ncell floats, output dloss/dlog(n_H0) per cell (overwritten);
  *   d_dL:         device, n_src doubles, output dloss/dL per source (overwritten), or NULL.
- * Split points and tau_max retirement are held fixed. Same parameters and status rules as
- * art_trace; h_stats as in art_trace. */
-int art_trace_backward(art_grid* g, const art_params* p, const float* d_w, float* d_dlog_nH0,
-                       double* d_dL, art_stats* h_stats);
+ * Split points and tau_max retirement are held fixed. A force term doubles the per-step
+ * gather (32-byte cell records, 32 B x ncell of library memory). One-bin traces only
+ * (ART_EINVAL with a second bin). Same parameters and status rules as art_trace; h_stats
+ * as in art_trace. */
+int art_trace_backward(art_grid* g, const art_params* p, const float* d_w, const float* d_v,
+                       float* d_dlog_nH0, double* d_dL, art_stats* h_stats);
 
 /* Neutral-fraction update of every cell over dt (Sec. 2.3), elementwise on the stream:
  *   method 0: Eq. e:xn3 (electron density held at n_H (1 - x_n) over the step);

@@ -116,7 +116,7 @@ def lib():
         L.art_trace.restype = i
         L.art_get_stats.argtypes = [vp, P(ArtStats)]
         L.art_get_stats.restype = i
-        L.art_trace_backward.argtypes = [vp, P(ArtParams), vp, vp, vp, P(ArtStats)]
+        L.art_trace_backward.argtypes = [vp, P(ArtParams), vp, vp, vp, vp, P(ArtStats)]
         L.art_trace_backward.restype = i
         L.art_xn_update.argtypes = [vp, ll, vp, vp, vp, vp, d, d, i]
         L.art_xn_update.restype = i

@@ -167,14 +167,19 @@ class Grid:
         C.check(C.lib().art_get_stats(self._h, ctypes.byref(st)), "art_get_stats")
         return st.as_dict()
 
-    def trace_backward(self, params: Params, w: torch.Tensor, stats: bool = True):
-        """Gradient of sum(w * gamma) w.r.t. log n_H0 (per cell) and L (per source)."""
+    def trace_backward(self, params: Params, w: torch.Tensor | None, stats: bool = True,
+                       v: torch.Tensor | None = None):
+        """Gradient of sum(w * gamma) + sum(v * force) w.r.t. log n_H0 (per cell) and L (per
+        source). w: (nz, ny, nx) or None; v: (3, nz, ny, nx) or None; not both None."""
         grad = torch.empty(self.shape, device=self.device, dtype=torch.float32)
         dL = torch.empty(self.nsrc, device=self.device, dtype=torch.float64)
         st = C.ArtStats()
         cp = params.to_c()
-        rc = C.lib().art_trace_backward(self._h, ctypes.byref(cp), _dev_ptr(w.contiguous(), "w"),
-                                        _dev_ptr(grad, "grad"), ctypes.c_void_p(dL.data_ptr()),
+        wc = None if w is None else w.float().contiguous()
+        vc = None if v is None else v.float().contiguous()
+        rc = C.lib().art_trace_backward(self._h, ctypes.byref(cp), _dev_ptr(wc, "w"),
+                                        _dev_ptr(vc, "v"), _dev_ptr(grad, "grad"),
+                                        ctypes.c_void_p(dL.data_ptr()),
                                         ctypes.byref(st) if stats else None)
         C.check(rc, "art_trace_backward")
         return grad, dL, (st.as_dict() if stats else None)
@@ -208,28 +213,34 @@ def dt_substep(gamma: torch.Tensor, nH: torch.Tensor, xn: torch.Tensor, alpha_B:
 
 
 class ARTFunction(torch.autograd.Function):
-    """gamma = ART(log n_H0, L): forward trace, hand-written adjoint in ``backward``.
+    """gamma = ART(log n_H0, L), or (gamma, force) with ``with_force``: forward trace,
+    hand-written adjoint in ``backward``.
 
     Inputs: log_nH0 (nz,ny,nx) float32 CUDA, L (n_src,) float64 (any device); ``grid`` is a
     Grid whose sources sit at the positions to trace (their luminosities are replaced by L);
-    ``params`` the trace parameters. Only gamma carries a gradient.
+    ``params`` the trace parameters. gamma and force carry gradients.
     """
 
     @staticmethod
     def forward(ctx, log_nH0: torch.Tensor, L: torch.Tensor, grid: Grid, params: Params,
-                positions):
+                positions, with_force: bool = False):
         nH0 = torch.exp(log_nH0.detach()).contiguous()
         grid.update_fields(nH0)
         grid.clear_sources()
         grid.add_sources(positions, L.detach().double().cpu().numpy())
-        out = grid.trace(params, force=False, stats=False)
+        out = grid.trace(params, force=with_force, stats=False)
         ctx.grid, ctx.params, ctx.nH0 = grid, params, nH0
         ctx.L_device = L.device
+        ctx.with_force = with_force
+        if with_force:
+            return out["gamma"], out["force"]
         return out["gamma"]
 
     @staticmethod
-    def backward(ctx, dgamma: torch.Tensor):
+    def backward(ctx, dgamma: torch.Tensor, dforce: torch.Tensor | None = None):
         grid = ctx.grid
         grid.update_fields(ctx.nH0)
-        grad, dL, _ = grid.trace_backward(ctx.params, dgamma.float().contiguous(), stats=False)
-        return grad, dL.to(ctx.L_device), None, None, None
+        if dgamma is None and dforce is None:
+            return None, None, None, None, None, None
+        grad, dL, _ = grid.trace_backward(ctx.params, dgamma, stats=False, v=dforce)
+        return grad, dL.to(ctx.L_device), None, None, None, None

@@ -1,13 +1,15 @@
-// art_adjoint.cu -- hand-written adjoint of the forward trace for loss = sum_c w_c gamma_c
-// (new; the paper has no adjoint). Gradients with respect to log n_H0 per cell and to every
-// source luminosity.
+// art_adjoint.cu -- hand-written adjoint of the forward trace for
+// loss = sum_c (w_c gamma_c + v_c . force_c) (new; the paper has no adjoint). Gradients with
+// respect to log n_H0 per cell and to every source luminosity.
 //
-// For a segment j of a ray in cell c, with G_j = L_in ds phi(dtau), dtau = chi ds and
-// dtauH = n_H0 sigma_H ds (the part of dtau that scales with n_H0):
-//   d loss / d log n_H0[c] += dtauH (w_c k L_in ds phi'(dtau) - S_after(j)),
-// where k converts G to gamma and S_after(j) is the weighted sum w k G over every later
-// segment of the ray and over all of its descendants (their entering luminosity carries the
-// factor e^-dtau of segment j). Split points and tau_max retirement are held fixed.
+// For a segment j of a ray in cell c, with G_j = L_in ds phi(dtau), dL_j = L_in (1 - e^-dtau),
+// dtau = chi ds and dtauH = n_H0 sigma_H ds (the part of dtau that scales with n_H0), the
+// segment adds w_c k G_j + q_j dL_j to the loss (k converts G to gamma, q_j = (v_c . n)/dV)
+// and
+//   d loss / d log n_H0[c] += dtauH (w_c k L_in ds phi'(dtau) + q_j L_in e^-dtau - S_after(j)),
+// where S_after(j) is the loss of every later segment of the ray and of all of its
+// descendants (their entering luminosity carries the factor e^-dtau of segment j). Split
+// points and tau_max retirement are held fixed.
 //
 // Nothing is stored per segment. Rays are traced with unit source luminosity (the loss is
 // linear in each L_s; gradients are scaled by L_s when deposited) in the deepest-first phases
@@ -52,6 +54,24 @@ __device__ __forceinline__ float dphi_of(float x, float em)
     return ((1.f + x) * (1.f + em) - 1.f) / (x * x);
 }
 
+// Running sum in two floats without renormalisation: hi + g is split exactly (two-sum) and
+// its rounding error collected in lo.
+__device__ __forceinline__ df df_acc(df a, float g)
+{
+    const df s = df_two_sum(a.hi, g);
+    return {s.hi, a.lo + s.lo};
+}
+
+// a - g for a remainder that only decreases (a >= g >= 0): with |hi| >= g the error of
+// hi - g is exact by the fast two-sum; where rounding of earlier steps left hi just below g,
+// hi - g is itself exact (Sterbenz) and the error is 0.
+__device__ __forceinline__ df df_dec(df a, float g)
+{
+    const float s = a.hi - g;
+    const float e = (a.hi - s) - g;
+    return {s, a.lo + e};
+}
+
 // Per-lane sum of dloss/dL for the source of the lane's recent rays, flushed to the global
 // FP64 sum when the lane moves to another source (rays of one source are consecutive).
 struct DLacc {
@@ -74,6 +94,19 @@ __device__ __forceinline__ void red_f32(float* p, float v)
     asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
 
+// The {chi, chi_H, w, 0} part of a reverse-sweep cell record, and the force weight of the
+// segment: q = (v . n) / dV, so that the segment adds q dL to the loss (0 without a force term).
+__device__ __forceinline__ float4 rec_main(const float4& c) { return c; }
+__device__ __forceinline__ float4 rec_main(const CellF& c) { return c.a; }
+__device__ __forceinline__ float force_weight(const float4&, const float*, float) { return 0.f; }
+__device__ __forceinline__ float force_weight(const CellF& c, const float* n, float fs)
+{
+    return fs * fmaf(c.b.x, n[0], fmaf(c.b.y, n[1], c.b.z * n[2]));
+}
+template <class Cell> __device__ __forceinline__ const Cell* recs_of(const TraceArgs& A);
+template <> __device__ __forceinline__ const float4* recs_of<float4>(const TraceArgs& A) { return A.rec; }
+template <> __device__ __forceinline__ const CellF* recs_of<CellF>(const TraceArgs& A) { return A.recf; }
+
 // One expand phase of the reverse sweep on the rays in slots [cursor .. end) of level l
 // (phase starting at slot `begin`). Pass 1 walks each ray for its own weighted sum. A ray
 // that splits stores that sum, a pending-children count of 4 and its children (in order, as
@@ -83,9 +116,11 @@ __device__ __forceinline__ void red_f32(float* p, float v)
 // phase's), and so on towards the base level: no separate collapse phase is needed, because
 // the deepest-first schedule does not reuse a level's slots before everything below it has
 // finished. Warp-uniform.
+template <class Cell>
 __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* cursor,
                             unsigned long long begin, unsigned long long end, Tally& T, DLacc& D)
 {
+    const Cell* const recs = recs_of<Cell>(A);
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt = (1u << lane) - 1u;
     const LevelInfo LV = A.levels[l];
@@ -101,7 +136,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
     bool more = true;
     int mode = 0;          // 0 idle, 1 pass 1 (level l), 2 pass 2 (level lv <= l)
     int lv = l;            // level of the ray being walked
-    WalkT<float4> W;
+    WalkT<Cell> W;
     unsigned s = 0, p = 0;
     unsigned slot = 0;
     float L0 = 0.f, Ls = 0.f;
@@ -134,7 +169,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
             total = rem.hi + rem.lo;
             const LevelInfo Lp = A.levels[lv];
             rmax = Lp.rmax;
-            ray_begin(A, Lp, Pl, lv, slot, W, A.rec, s, p, L0, splits);
+            ray_begin(A, Lp, Pl, lv, slot, W, recs, s, p, L0, splits);
             Ls = __ldg(A.srcL + s);
             mode = 2;
             return;
@@ -159,7 +194,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
                     slot = wnext + rank;
                     lv = l;
                     rmax = LV.rmax;
-                    const int st = ray_begin(A, LV, B, l, slot, W, A.rec, s, p, L0, splits);
+                    const int st = ray_begin(A, LV, B, l, slot, W, recs, s, p, L0, splits);
                     if (st > 0) {
                         Ls = __ldg(A.srcL + s);
                         mode = 1;
@@ -189,18 +224,24 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
 #pragma unroll 1
         for (int k = 0; k < 8; ++k) {
             if (mode != 0) {
-                const float wv = W.cell.z;   // weight and neutral-H opacity of this cell
-                const float hv = W.cell.y;
-                const StepOut o = walk_step<false>(W, splits, rmax, sy, sz, A.rec, A.tau_max);
-                const float g = wv * gs * o.G;
+                const float4 cm = rec_main(W.cell);
+                const float wv = cm.z;   // weight and neutral-H opacity of this cell
+                const float hv = cm.y;
+                const float q = force_weight(W.cell, W.n, A.fscale);
+                const StepOut o = walk_step<false>(W, splits, rmax, sy, sz, recs, A.tau_max);
+                // this segment's loss: w k G, plus q dL with a force term
+                const float g = fmaf(q, o.dL, wv * gs * o.G);
                 if (mode == 1) {
-                    own = df_add(own, {g, 0.f});
+                    own = df_acc(own, g);
                     ncross += o.cell >= 0 ? 1u : 0u;
                 } else {
-                    rem = df_add(rem, {-g, 0.f});
+                    rem = df_dec(rem, g);
                     const float after = rem.hi + rem.lo;
                     const float dphi = dphi_of(o.dtau, -o.dtau * o.phi);
-                    const float val = Ls * hv * o.ds * (wv * gs * o.Lin * o.ds * dphi - after);
+                    // d(segment loss)/d dtau: w k L_in ds phi' + q L_in e^-dtau (W.L is now
+                    // L_in e^-dtau)
+                    const float own_d = fmaf(q, W.L, wv * gs * o.Lin * o.ds * dphi);
+                    const float val = Ls * hv * o.ds * (own_d - after);
                     if (o.cell >= 0) red_f32(A.grad + o.cell, val);
                 }
                 if (o.ev != EV_NONE) {
@@ -232,7 +273,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
                             // a leaf: pass 2 right away
                             total = own.hi + own.lo;
                             rem = own;
-                            ray_begin(A, LV, B, l, slot, W, A.rec, s, p, L0, splits);
+                            ray_begin(A, LV, B, l, slot, W, recs, s, p, L0, splits);
                             mode = 2;
                         }
                     } else {
@@ -246,6 +287,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
     count_rays(A.stats, l, nrays);
 }
 
+template <class Cell>
 __global__ void __launch_bounds__(256, 4) k_backward_persistent(const __grid_constant__ TraceArgs A)
 {
     tally_init();
@@ -287,7 +329,7 @@ __global__ void __launch_bounds__(256, 4) k_backward_persistent(const __grid_con
         __syncthreads();
         const int l = s_level;
         if (l < 0) break;
-        run_adjoint(A, l, &sc->cursor[l], s_begin, s_end, T, D);
+        run_adjoint<Cell>(A, l, &sc->cursor[l], s_begin, s_end, T, D);
     }
     if (D.src != 0xffffffffu && D.v.hi != 0.f) atomicAdd(A.dL + D.src, (double)D.v.hi + (double)D.v.lo);
     tally_flush(A.stats);
@@ -300,7 +342,20 @@ __global__ void k_pack_cells(long long ncell, const float* __restrict__ chi,
 {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long step = (long long)gridDim.x * blockDim.x;
-    for (; i < ncell; i += step) rec[i] = make_float4(chi[i], chiH[i], w[i], 0.f);
+    for (; i < ncell; i += step) rec[i] = make_float4(chi[i], chiH[i], w ? w[i] : 0.f, 0.f);
+}
+
+// The same with the force weight v (3 blocks of ncell floats: x, y, z).
+__global__ void k_pack_cells_f(long long ncell, const float* __restrict__ chi,
+                               const float* __restrict__ chiH, const float* __restrict__ w,
+                               const float* __restrict__ v, CellF* __restrict__ rec)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long step = (long long)gridDim.x * blockDim.x;
+    for (; i < ncell; i += step) {
+        rec[i].a = make_float4(chi[i], chiH[i], w ? w[i] : 0.f, 0.f);
+        rec[i].b = make_float4(v[i], v[ncell + i], v[2 * ncell + i], 0.f);
+    }
 }
 
 __global__ void k_inject_all(int nsrc, unsigned npix0, RayBuf B, unsigned long long* count)
@@ -325,9 +380,10 @@ int status_of(cudaError_t e)
 }  // namespace
 
 extern "C" int art_trace_backward(art_grid* g, const art_params* p, const float* d_w,
-                                  float* d_dlog_nH0, double* d_dL, art_stats* h_stats)
+                                  const float* d_v, float* d_dlog_nH0, double* d_dL,
+                                  art_stats* h_stats)
 {
-    if (!g || !d_w || !d_dlog_nH0) return ART_EINVAL;
+    if (!g || (!d_w && !d_v) || !d_dlog_nH0) return ART_EINVAL;
     int rc = check_params(p);
     if (rc) return rc;
     // the reverse sweep always runs the persistent schedule (all base rays in one buffer)
@@ -345,7 +401,9 @@ extern "C" int art_trace_backward(art_grid* g, const art_params* p, const float*
     if (rc) return rc;
     if ((size_t)ns > g->srcL_cap) {
         if (g->d_srcL) cudaFree(g->d_srcL);
+        if (g->d_dL_scratch) cudaFree(g->d_dL_scratch);
         g->d_srcL = nullptr;
+        g->d_dL_scratch = nullptr;
         g->srcL_cap = 0;
         if ((rc = status_of(cudaMalloc((void**)&g->d_srcL, sizeof(float) * ns)))) return rc;
         if ((rc = status_of(cudaMalloc((void**)&g->d_dL_scratch, sizeof(double) * ns)))) return rc;
@@ -366,27 +424,33 @@ extern "C" int art_trace_backward(art_grid* g, const art_params* p, const float*
     k_inject_all<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(ns, npix0, g->buf[l0],
                                                             &g->d_sched->count[l0]);
     if ((rc = status_of(cudaGetLastError()))) return rc;
-    if (!g->d_rec && (rc = status_of(cudaMalloc((void**)&g->d_rec, sizeof(float4) * g->ncell))))
-        return rc;
-    {
-        const int blocks = (int)std::min<long long>((g->ncell + 255) / 256, (long long)g->sms * 16);
-        k_pack_cells<<<blocks, 256, 0, st>>>(g->ncell, g->d_chi, g->d_chiH, d_w, g->d_rec);
-        if ((rc = status_of(cudaGetLastError()))) return rc;
+    const int pack_blocks = (int)std::min<long long>((g->ncell + 255) / 256, (long long)g->sms * 16);
+    if (d_v) {
+        if (!g->d_recf && (rc = status_of(cudaMalloc((void**)&g->d_recf, sizeof(CellF) * g->ncell))))
+            return rc;
+        k_pack_cells_f<<<pack_blocks, 256, 0, st>>>(g->ncell, g->d_chi, g->d_chiH, d_w, d_v, g->d_recf);
+    } else {
+        if (!g->d_rec && (rc = status_of(cudaMalloc((void**)&g->d_rec, sizeof(float4) * g->ncell))))
+            return rc;
+        k_pack_cells<<<pack_blocks, 256, 0, st>>>(g->ncell, g->d_chi, g->d_chiH, d_w, g->d_rec);
     }
+    if ((rc = status_of(cudaGetLastError()))) return rc;
     TraceArgs A = make_args(g, p);
     if (p->chunk == 0) A.chunk = 32;  // measured best for the reverse sweep (64 for the forward)
     A.rec = g->d_rec;
+    A.recf = d_v ? g->d_recf : nullptr;
     A.w = d_w;
     A.grad = d_dlog_nH0;
     A.dL = dL;
     A.srcL = g->d_srcL;
     const double dV = g->dx * g->dx * g->dx;
     A.gscale = (float)(p->sigma_H * g->dx / dV);
+    A.fscale = (float)(1.0 / dV);
     // the reverse sweep is compiled for blocks of at most 256 threads (register budget)
     const int threads = p->block_threads > 0 && p->block_threads < 256 ? p->block_threads : 256;
+    void (*kern)(TraceArgs) = d_v ? k_backward_persistent<CellF> : k_backward_persistent<float4>;
     int per_sm = 0;
-    if ((rc = status_of(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_persistent,
-                                                                      threads, 0))))
+    if ((rc = status_of(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0))))
         return rc;
     if (per_sm < 1) return ART_EINVAL;
     cudaLaunchConfig_t cfg;
@@ -399,7 +463,7 @@ extern "C" int art_trace_backward(art_grid* g, const art_params* p, const float*
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if ((rc = status_of(cudaLaunchKernelEx(&cfg, k_backward_persistent, A)))) return rc;
+    if ((rc = status_of(cudaLaunchKernelEx(&cfg, kern, A)))) return rc;
     if ((rc = status_of(cudaMemcpyAsync(g->h_stats, g->d_stats, sizeof(DevStats),
                                         cudaMemcpyDeviceToHost, st))))
         return rc;

@@ -135,6 +135,8 @@ struct Sched {
 };
 
 // Everything the trace kernels read.
+struct CellF;
+
 struct TraceArgs {
     int nx, ny, nz;
     int level0, lmax_glob;
@@ -157,6 +159,8 @@ struct TraceArgs {
     long long wait_ns;       // bound of a grid-barrier wait (<0: give up at once)
     float gscale;            // adjoint: sigma_H * dx / dV (gamma per unit G)
     const float* srcL;       // adjoint: source luminosities (gradients scale with them)
+    const CellF* recf;       // adjoint with a force term: per cell {chi, chi_H, w, 0}, {v, 0}
+    float fscale;            // adjoint: force per unit momentum (1 / dV)
 };
 
 enum : int { EV_NONE = 0, EV_EXIT = 1, EV_DROP = 2, EV_SPLIT = 3 };
@@ -179,6 +183,17 @@ template <class Cell> __device__ __forceinline__ Cell cell_zero();
 template <> __device__ __forceinline__ float cell_zero<float>() { return 0.f; }
 template <> __device__ __forceinline__ float4 cell_zero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 template <> __device__ __forceinline__ float2 cell_zero<float2>() { return make_float2(0.f, 0.f); }
+// Cell record of a reverse sweep whose loss has a force term: {chi, chi_H, w, 0} and the
+// force weight {v_x, v_y, v_z, 0} (32 bytes, two 16-byte gathers per step).
+struct CellF {
+    float4 a, b;
+};
+__device__ __forceinline__ float chi_of(const CellF& c) { return c.a.x; }
+__device__ __forceinline__ CellF load_cell(const CellF* p) { return {__ldg(&p->a), __ldg(&p->b)}; }
+template <> __device__ __forceinline__ CellF cell_zero<CellF>()
+{
+    return {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+}
 
 template <class Cell>
 struct WalkT {
@@ -243,26 +258,22 @@ struct StepOut {
     int ev;
 };
 
-// (1 - e^-x)/x for x >= 0: Taylor series below 1 (no cancellation), exponential above.
-// Both branches are evaluated and one is selected, so lanes never diverge here.
+// (1 - e^-x)/x for x >= 0. Below 1 as e^{-x/2} sinh(x/2)/(x/2), the even series of
+// sinh(y)/y to y^8 (truncation < 3e-11 for y < 1/2, no cancellation); above 1 as
+// (1 - e^{-x})/x with e^{-x} = (e^{-x/2})^2. One exponential serves both branches, which are
+// evaluated and selected, so lanes never diverge here.
 __device__ __forceinline__ float phi_of(float x)
 {
-    const float xs = fminf(x, 1.f);
-    float r = -1.f / 479001600.f;          // -1/12!
-    r = fmaf(r, xs, 1.f / 39916800.f);
-    r = fmaf(r, xs, -1.f / 3628800.f);
-    r = fmaf(r, xs, 1.f / 362880.f);
-    r = fmaf(r, xs, -1.f / 40320.f);
-    r = fmaf(r, xs, 1.f / 5040.f);
-    r = fmaf(r, xs, -1.f / 720.f);
-    r = fmaf(r, xs, 1.f / 120.f);
-    r = fmaf(r, xs, -1.f / 24.f);
-    r = fmaf(r, xs, 1.f / 6.f);
-    r = fmaf(r, xs, -0.5f);
-    r = fmaf(r, xs, 1.f);
-    const float xl = fmaxf(x, 1.f);
-    const float e = __fdividef(1.f - __expf(-xl), xl);
-    return x < 1.f ? r : e;
+    const float y = 0.5f * x;
+    const float E = __expf(-y);
+    const float y2 = y * y;
+    float S = fmaf(y2, 1.f / 362880.f, 1.f / 5040.f);
+    S = fmaf(S, y2, 1.f / 120.f);
+    S = fmaf(S, y2, 1.f / 6.f);
+    S = fmaf(S, y2, 1.f);
+    const float small = E * S;
+    const float large = __fdividef(fmaf(-E, E, 1.f), fmaxf(x, 1.f));
+    return x < 1.f ? small : large;
 }
 
 __device__ __forceinline__ df df_sel(bool c, df a, df b) { return {c ? a.hi : b.hi, c ? a.lo : b.lo}; }
@@ -490,7 +501,7 @@ __device__ __forceinline__ int ray_begin(const TraceArgs& A, const LevelInfo& LV
         W.Ln = (l == A.level0) ? __ldg(A.srcLn + s) : __ldcg(B.Ln + i);
         W.taun = (l == A.level0) ? 0.f : __ldcg(B.taun + i);
     }
-    W.cell = inside ? __ldg(cells + W.idx) : cell_zero<Cell>();
+    W.cell = inside ? load_cell(cells + W.idx) : cell_zero<Cell>();
     return inside ? 1 : 0;
 }
 

@@ -75,6 +75,7 @@ struct art_grid {
     // adjoint: source luminosities and a dL buffer for callers that pass none
     float* d_srcL = nullptr;
     float4* d_rec = nullptr;     // per-cell {chi, chi_H, w, 0} of the reverse sweep
+    art::CellF* d_recf = nullptr;  // the same with the force weight (loss with a force term)
     double* d_dL_scratch = nullptr;
     size_t srcL_cap = 0;
     std::vector<float> h_srcL;

@@ -83,6 +83,11 @@ def uniform_weights(n: int, seed: int) -> np.ndarray:
     return np.random.default_rng(seed).random((n, n, n))
 
 
+def force_weights(n: int, seed: int) -> np.ndarray:
+    """Loss weights of the force, v ~ U[-1, 1) per component, shape (3, n, n, n) (float64)."""
+    return np.random.default_rng(seed + 104729).uniform(-1.0, 1.0, size=(3, n, n, n))
+
+
 def random_rotation(seed: int) -> np.ndarray:
     """A uniformly random proper rotation matrix (row-major 3x3), via QR of a Gaussian matrix."""
     rng = np.random.default_rng(seed)

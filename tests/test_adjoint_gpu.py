@@ -106,3 +106,65 @@ def test_autograd_function_matches_backward(art):
     PA.compare_field(logn.grad.cpu().numpy(), rg, rel=3e-5, what="autograd grad")
     np.testing.assert_allclose(Lt.grad.numpy(), rdL, rtol=PA.REL)
     g.close()
+
+
+def _force_case(A, n, nsrc, seed, with_w=True):
+    rho = synth.lognormal_field(n, 1.5, seed=seed).astype(np.float32)
+    pos = synth.uniform_positions(nsrc, seed=seed)
+    L = synth.power_law_luminosities(nsrc, seed=seed)
+    w = (0.5 * synth.uniform_weights(n, seed=seed)).astype(np.float32) if with_w else None
+    v = synth.force_weights(n, seed=seed).astype(np.float32)
+    p = A.Params(level0=3, tau_max=30.0, sigma_H=10.0)
+    dev = torch.device("cuda")
+    g = A.Grid(torch.from_numpy(rho).to(dev), 1.0 / n)
+    g.add_sources(pos, L)
+    fwd = g.trace(p, force=True)
+    grad, dL, st = g.trace_backward(p, None if w is None else torch.from_numpy(w).to(dev),
+                                    v=torch.from_numpy(v).to(dev))
+    out = dict(grad=grad.cpu().numpy(), dL=dL.cpu().numpy(), stats=st,
+               gamma=fwd["gamma"].cpu().numpy(), force=fwd["force"].cpu().numpy())
+    g.close()
+    prob = O.Problem(nH0=rho, pos=pos, L=L, dx=1.0 / n, sigma_H=10.0, level0=3, tau_max=30.0)
+    ref = O.trace_adjoint(prob, np.zeros_like(rho) if w is None else w, v=v, nthreads=8)
+    return out, ref, w, v
+
+
+@pytest.mark.parametrize("with_w", [True, False], ids=["gamma_and_force", "force_only"])
+def test_adjoint_force_term(art, with_w):
+    """loss = sum w gamma + sum v . force with v of both signs (32-byte cell records)."""
+    out, (rg, rdL, rloss), w, v = _force_case(art, 48, 3, seed=13, with_w=with_w)
+    assert out["stats"]["status"] == 0
+    err = np.abs(out["grad"].astype(np.float64) - rg).max() / np.abs(rg).max()
+    assert err <= PA.REL, f"gradient with a force term: max-norm rel err {err:.3e}"
+    assert np.abs(out["dL"] - rdL).max() <= PA.REL * np.abs(rdL).max()
+    terms = (v.astype(np.float64) * out["force"].astype(np.float64))
+    gpu_loss = terms.sum()
+    scale = np.abs(terms).sum()
+    if w is not None:
+        gt = w.astype(np.float64) * out["gamma"].astype(np.float64)
+        gpu_loss += gt.sum()
+        scale += np.abs(gt).sum()
+    assert abs(gpu_loss - rloss) <= PA.REL * scale
+
+
+def test_autograd_function_with_force(art):
+    n = 32
+    rho = synth.lognormal_field(n, 1.5, seed=6).astype(np.float32)
+    pos = synth.uniform_positions(2, seed=6)
+    L = synth.power_law_luminosities(2, seed=6)
+    w = synth.uniform_weights(n, seed=6).astype(np.float32)
+    v = synth.force_weights(n, seed=6).astype(np.float32)
+    p = art.Params(level0=3, tau_max=30.0, sigma_H=8.0)
+    logn = torch.log(torch.from_numpy(rho).cuda()).requires_grad_(True)
+    Lt = torch.tensor(L, dtype=torch.float64, requires_grad=True)
+    g = art.Grid(torch.from_numpy(rho).cuda(), 1.0 / n)
+    gamma, force = art.ARTFunction.apply(logn, Lt, g, p, pos, True)
+    loss = (gamma.double() * torch.from_numpy(w).cuda().double()).sum() + \
+        (force.double() * torch.from_numpy(v).cuda().double()).sum()
+    loss.backward()
+    prob = O.Problem(nH0=rho, pos=pos, L=L, dx=1.0 / n, sigma_H=8.0, level0=3, tau_max=30.0)
+    rg, rdL, _ = O.trace_adjoint(prob, w, v=v, nthreads=8)
+    err = np.abs(logn.grad.cpu().numpy().astype(np.float64) - rg).max() / np.abs(rg).max()
+    assert err <= PA.REL
+    assert np.abs(Lt.grad.numpy() - rdL).max() <= PA.REL * np.abs(rdL).max()
+    g.close()
