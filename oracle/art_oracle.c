@@ -182,6 +182,7 @@ typedef struct {
     int use_rot;
     int two_bin;        /* a second, non-ionizing bin attenuated by dust only (Sec. 2.3) */
     double rmax_unit;   /* sqrt(3/(pi m_ray)): r_max(l) = rmax_unit * 2^l (cells) */
+    double dmax;        /* rays end at this distance from their source (cells); INFINITY: none */
 } or_problem;
 
 typedef struct {
@@ -273,7 +274,8 @@ enum { OR_END_EXIT = 0, OR_END_DROP = 1, OR_END_SPLIT = 2 };
 
 /*
  * Walk one ray (level, pixel, L, tau) from r_start to its end: the box exit, tau > tau_max,
- * or r_max(level) when level < lmax (Sec. 2.1). Face crossings are measured from the source
+ * r_max(level) when level < lmax (Sec. 2.1), or the cutoff distance d_max from the source
+ * (the terminated rays of the weak-scaling test, Sec. 3.1; reported like an exit). Face crossings are measured from the source
  * (t_a = (face_a - u_a)/n_a, never incremented), so no drift builds up. Calls deposit per
  * segment when acc != NULL, records segments when segs != NULL. Returns the end reason;
  * the ray's L and tau are updated to their values at the end.
@@ -295,7 +297,11 @@ static int or_walk(const or_problem* P, const double u[3], or_ray* ray, int lmax
     double n[3];
     or_direction(P, ray->level, ray->pix, n);
     const double r0 = ray->level > P->level0 ? or_rmax(P, ray->level - 1) : 0.0;
-    const double rend = ray->level < lmax ? or_rmax(P, ray->level) : INFINITY;
+    /* the walk ends at the split radius (levels below lmax) or at d_max, whichever comes
+     * first; at equal radii the cut wins (the ray is not split) */
+    const double rsplit = ray->level < lmax ? or_rmax(P, ray->level) : INFINITY;
+    const double rend = fmin(rsplit, P->dmax);
+    const int cut = P->dmax <= rsplit;
 
     int64_t c[3];
     double tn[3], dt[3];
@@ -360,7 +366,7 @@ static int or_walk(const or_problem* P, const double u[3], or_ray* ray, int lmax
         }
         if (rend <= tmin) {
             if (tmin - rend < OR_NEAR) *near = 1;
-            return OR_END_SPLIT;
+            return cut ? OR_END_EXIT : OR_END_SPLIT;
         }
         if (tmin - rend > -OR_NEAR && rend < INFINITY) *near = 1;
         /* step every axis whose crossing ties with the earliest one */
@@ -413,9 +419,10 @@ static void or_trace_tree(const or_problem* P, const double u[3], int lmax, int 
 
 static int or_setup(or_problem* P, int nx, int ny, int nz, double dx, const float* nH0,
                     const float* nH, int level0, int level_cap, double m_ray, double tau_max,
-                    double sigma_H, double sigma_d, const double* rot)
+                    double sigma_H, double sigma_d, const double* rot, double d_max)
 {
     if (nx <= 0 || ny <= 0 || nz <= 0 || !(dx > 0) || !nH0) return -1;
+    if (d_max != d_max) return -1;
     if (level0 < 0 || level0 > 12 || !(m_ray > 0) || !(tau_max > 0)) return -1;
     if (level_cap >= 0 && (level_cap < level0 || level_cap > OR_MAX_LEVEL)) return -1;
     P->n[0] = nx; P->n[1] = ny; P->n[2] = nz;
@@ -427,6 +434,7 @@ static int or_setup(or_problem* P, int nx, int ny, int nz, double dx, const floa
     P->two_bin = 0;
     for (int i = 0; i < 9; ++i) P->rot[i] = rot ? rot[i] : (i % 4 == 0 ? 1.0 : 0.0);
     P->rmax_unit = sqrt(3.0 / (M_PI * m_ray));
+    P->dmax = d_max > 0.0 ? d_max / dx : INFINITY;
     return 0;
 }
 
@@ -454,11 +462,12 @@ int or_trace(int nx, int ny, int nz, const double* lo, double dx, const float* n
              const float* nH, int nsrc, const double* pos, const double* L, const double* Ln,
              int level0,
              int level_cap, double m_ray, double tau_max, double sigma_H, double sigma_d,
-             const double* rot, double* acc, double* dstat, long long* istat, int nthreads)
+             const double* rot, double d_max, double* acc, double* dstat, long long* istat,
+             int nthreads)
 {
     or_problem P;
     if (or_setup(&P, nx, ny, nz, dx, nH0, nH, level0, level_cap, m_ray, tau_max, sigma_H,
-                 sigma_d, rot))
+                 sigma_d, rot, d_max))
         return -1;
     if (nsrc < 0) return -1;
     P.two_bin = Ln != NULL;
@@ -554,13 +563,13 @@ int or_trace(int nx, int ny, int nz, const double* lo, double dx, const float* n
  */
 int or_ray_segments(int nx, int ny, int nz, const double* lo, double dx, const float* nH0,
                     const float* nH, const double* pos, int level0, int level_cap, double m_ray,
-                    double tau_max, double sigma_H, double sigma_d, const double* rot, int level,
-                    unsigned long long pix, double L, double tau, long long* cells, double* ds,
-                    int cap, int* end_reason)
+                    double tau_max, double sigma_H, double sigma_d, const double* rot,
+                    double d_max, int level, unsigned long long pix, double L, double tau,
+                    long long* cells, double* ds, int cap, int* end_reason)
 {
     or_problem P;
     if (or_setup(&P, nx, ny, nz, dx, nH0, nH, level0, level_cap, m_ray, tau_max, sigma_H,
-                 sigma_d, rot))
+                 sigma_d, rot, d_max))
         return -1;
     double u[3];
     if (or_source_cells(&P, 1, lo, pos, u)) return -1;
@@ -651,12 +660,12 @@ static double or_adjoint_tree(const or_problem* P, const double u[3], int lmax, 
 int or_trace_adjoint(int nx, int ny, int nz, const double* lo, double dx, const float* nH0,
                      const float* nH, int nsrc, const double* pos, const double* L, int level0,
                      int level_cap, double m_ray, double tau_max, double sigma_H, double sigma_d,
-                     const double* rot, const double* w, const double* v, double* grad,
-                     double* dL, double* loss, int nthreads)
+                     const double* rot, double d_max, const double* w, const double* v,
+                     double* grad, double* dL, double* loss, int nthreads)
 {
     or_problem P;
     if (or_setup(&P, nx, ny, nz, dx, nH0, nH, level0, level_cap, m_ray, tau_max, sigma_H,
-                 sigma_d, rot))
+                 sigma_d, rot, d_max))
         return -1;
     double* u = (double*)malloc(sizeof(double) * 3 * (size_t)(nsrc > 0 ? nsrc : 1));
     if (or_source_cells(&P, nsrc, lo, pos, u)) { free(u); return -1; }

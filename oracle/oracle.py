@@ -48,13 +48,13 @@ def _load():
         lib.or_vec2pix.argtypes = [i, dp]
         lib.or_vec2pix.restype = ctypes.c_uint64
         lib.or_trace.argtypes = [i, i, i, dp, d, fp, fp, i, dp, dp, dp, i, i, d, d, d, d, dp,
-                                 dp, dp, lp, i]
+                                 d, dp, dp, lp, i]
         lib.or_trace.restype = i
-        lib.or_ray_segments.argtypes = [i, i, i, dp, d, fp, fp, dp, i, i, d, d, d, d, dp, i,
-                                        ctypes.c_ulonglong, d, d, lp, dp, i, P(ctypes.c_int)]
+        lib.or_ray_segments.argtypes = [i, i, i, dp, d, fp, fp, dp, i, i, d, d, d, d, dp, d,
+                                        i, ctypes.c_ulonglong, d, d, lp, dp, i, P(ctypes.c_int)]
         lib.or_ray_segments.restype = i
         lib.or_trace_adjoint.argtypes = [i, i, i, dp, d, fp, fp, i, dp, dp, i, i, d, d, d, d,
-                                         dp, dp, dp, dp, dp, dp, i]
+                                         dp, d, dp, dp, dp, dp, dp, i]
         lib.or_trace_adjoint.restype = i
         _lib = lib
     return _lib
@@ -82,6 +82,7 @@ class Problem:
     tau_max: float = 30.0
     rot: np.ndarray | None = None
     Ln: np.ndarray | None = None          # non-ionizing luminosities: a second, dust-only bin
+    d_max: float = 0.0                    # rays end this far from their source (> 0), else none
 
     def _args(self):
         nz, ny, nx = self.nH0.shape
@@ -149,7 +150,7 @@ def trace(prob: Problem, nthreads: int = 1) -> TraceResult:
                       _ptr(prob._L, ctypes.c_double), _ptr(prob._Ln, ctypes.c_double),
                       prob.level0, prob.level_cap,
                       prob.m_ray, prob.tau_max, prob.sigma_H, prob.sigma_d,
-                      _ptr(prob._rot, ctypes.c_double), _ptr(acc, ctypes.c_double),
+                      _ptr(prob._rot, ctypes.c_double), prob.d_max, _ptr(acc, ctypes.c_double),
                       _ptr(dstat, ctypes.c_double), _ptr(istat, ctypes.c_longlong), nthreads)
     if rc != 0:
         raise ValueError("oracle rejected the problem")
@@ -167,7 +168,7 @@ def trace(prob: Problem, nthreads: int = 1) -> TraceResult:
 def ray_segments(prob: Problem, level: int, pix: int, L: float = 1.0, tau: float = 0.0,
                  cap: int = 1 << 20):
     """Cells and physical lengths of the segments of one ray of source 0; and the end reason
-    (0 exit, 1 tau_max, 2 split)."""
+    (0 exit or d_max cutoff, 1 tau_max, 2 split)."""
     lib = _load()
     nx, ny, nz = prob._args()
     cells = np.zeros(cap, dtype=np.int64)
@@ -177,7 +178,8 @@ def ray_segments(prob: Problem, level: int, pix: int, L: float = 1.0, tau: float
                             _ptr(prob._nH0, ctypes.c_float), _ptr(prob._nH, ctypes.c_float),
                             _ptr(prob._pos[:1].copy(), ctypes.c_double), prob.level0,
                             prob.level_cap, prob.m_ray, prob.tau_max, prob.sigma_H,
-                            prob.sigma_d, _ptr(prob._rot, ctypes.c_double), level, pix, L, tau,
+                            prob.sigma_d, _ptr(prob._rot, ctypes.c_double), prob.d_max, level,
+                            pix, L, tau,
                             _ptr(cells, ctypes.c_longlong), _ptr(ds, ctypes.c_double), cap,
                             ctypes.byref(end))
     if n < 0:
@@ -208,7 +210,8 @@ def trace_adjoint(prob: Problem, w: np.ndarray, nthreads: int = 1, v: np.ndarray
                               len(prob._L), _ptr(prob._pos, ctypes.c_double),
                               _ptr(prob._L, ctypes.c_double), prob.level0, prob.level_cap,
                               prob.m_ray, prob.tau_max, prob.sigma_H, prob.sigma_d,
-                              _ptr(prob._rot, ctypes.c_double), _ptr(w64, ctypes.c_double),
+                              _ptr(prob._rot, ctypes.c_double), prob.d_max,
+                              _ptr(w64, ctypes.c_double),
                               _ptr(v64, ctypes.c_double), _ptr(grad, ctypes.c_double),
                               _ptr(dL, ctypes.c_double), ctypes.byref(loss), nthreads)
     if rc != 0:

@@ -248,3 +248,65 @@ def test_two_bin_drop_uses_the_dust_depth():
     assert two.dropped <= math.exp(-3.0 * 44.0 / 4.0) * two.L_in
     assert two.absorbed + two.escaped + two.dropped == pytest.approx(1.0, rel=1e-12)
     assert two.absorbed_n + two.escaped_n + two.dropped_n == pytest.approx(1.0, rel=1e-12)
+
+
+# --- the d_max cutoff (rays terminated at a distance from their source, Sec. 3.1) ----------
+
+def test_dmax_beyond_the_box_changes_nothing():
+    from paper_1711_06277_gb300 import synth
+    n = 16
+    rho = synth.lognormal_field(n, 1.5, seed=7).astype(np.float32).astype(np.float64)
+    pos = synth.uniform_positions(3, seed=7)
+    base = dict(nH0=rho, pos=pos, L=[1.0, 0.5, 0.25], sigma_H=6.0, level0=2)
+    r0 = O.trace(_prob(n, **base))
+    r1 = O.trace(_prob(n, **base, d_max=2.0))  # farther than any box corner (sqrt 3)
+    assert np.array_equal(r0.G, r1.G) and np.array_equal(r0.F, r1.F)
+    assert (r0.escaped, r0.dropped, r0.crossings) == (r1.escaped, r1.dropped, r1.crossings)
+
+
+def test_dmax_uniform_medium_closed_form():
+    """Every path from the source is cut at d_max inside the box, whatever its splits: the
+    absorbed share is 1 - e^{-chi d_max}, the rest leaves as cut (counted as escaped)."""
+    n = 24
+    chi = 3.0
+    dmax = 7.3 / n
+    prob = _prob(n, nH0=np.full((n, n, n), chi), pos=[[0.5 + 0.1 / n, 0.5 - 0.2 / n, 0.5]],
+                 L=[2.0], level0=1, sigma_H=1.0, d_max=dmax)
+    r = O.trace(prob)
+    want = 2.0 * -math.expm1(-chi * dmax)
+    assert r.absorbed == pytest.approx(want, rel=1e-12)
+    assert r.escaped == pytest.approx(2.0 - want, rel=1e-12)
+    assert r.dropped == 0.0
+    # every split radius below d_max is used: levels 1-3 split (r_max 0.98, 1.95, 3.9 cells),
+    # level 4 (r_max 7.8 > 7.3) is cut at d_max, so no level-5 rays
+    assert r.rays_per_level[1:6].tolist() == [48, 192, 768, 3072, 0]
+    assert r.destroy == r.destroy_expected
+
+
+def test_dmax_leaves_far_cells_empty_and_cuts_paths_exactly():
+    n = 20
+    u = np.array([9.3, 10.6, 8.2])
+    dmax_cells = 5.25
+    prob = _prob(n, pos=[u / n], level0=2, level_cap=2, d_max=dmax_cells / n)
+    r = O.trace(prob)
+    k, j, i = np.indices((n, n, n))
+    # nearest point of each cell to the source
+    near = np.sqrt(sum(np.maximum(0.0, np.maximum(c - x, x - c - 1.0)) ** 2
+                       for c, x in ((i, u[0]), (j, u[1]), (k, u[2]))))
+    assert np.all(r.G[near > dmax_cells + 1e-9] == 0.0)
+    # vacuum: the path sum rule with every ray cut at d_max
+    assert float(r.G.sum()) == pytest.approx(dmax_cells / n, rel=1e-12)
+    cells, ds, end = O.ray_segments(prob, 2, 77)
+    assert end == 0 and ds.sum() * n == pytest.approx(dmax_cells, rel=1e-12)
+
+
+def test_dmax_equal_to_a_split_radius_cuts():
+    """d_max exactly at r_max(l): the cut wins and level l + 1 gets no rays."""
+    n = 32
+    m_ray = 4.0
+    r3 = math.sqrt(3.0 / (math.pi * m_ray)) * 2**3   # r_max(3) in cells
+    prob = _prob(n, pos=[[0.5 + 0.2 / n, 0.5 + 0.3 / n, 0.5 - 0.1 / n]], level0=2,
+                 d_max=r3 / n, m_ray=m_ray)
+    r = O.trace(prob)
+    assert r.rays_per_level[2:5].tolist() == [192, 768, 0]
+    assert r.escaped == pytest.approx(1.0, rel=1e-13)
