@@ -74,6 +74,10 @@ typedef struct {
                             (10 s); a negative value makes every wait give up at once */
     int blocks_per_sm;   /* resident blocks per SM of the persistent trace (0 = as many as
                             fit); fewer blocks keep fewer rays in flight */
+    double d_max;        /* > 0: every ray ends at this distance from its source (the cutoff
+                            of the weak-scaling test, Sec. 3.1), its remaining L counted as
+                            escaped; at d_max = r_max(l) the cut wins over the split.
+                            <= 0: no cutoff (default). NaN or inf: ART_EINVAL */
 } art_params;
 
 /* Counters of one trace (tallies in FP64). */

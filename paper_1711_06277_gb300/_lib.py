@@ -49,6 +49,7 @@ class ArtParams(ctypes.Structure):
         ("queue_capacity", ctypes.c_longlong),
         ("wait_limit_s", ctypes.c_double),
         ("blocks_per_sm", ctypes.c_int),
+        ("d_max", ctypes.c_double),
     ]
 
 

@@ -33,6 +33,7 @@ class Params:
     queue_capacity: int = 0
     wait_limit_s: float = 0.0
     blocks_per_sm: int = 0
+    d_max: float = 0.0                    # > 0: rays end this far from their source (Sec. 3.1)
 
     def to_c(self) -> C.ArtParams:
         p = C.ArtParams()
@@ -54,6 +55,7 @@ class Params:
         p.queue_capacity = int(self.queue_capacity)
         p.wait_limit_s = float(self.wait_limit_s)
         p.blocks_per_sm = int(self.blocks_per_sm)
+        p.d_max = float(self.d_max)
         return p
 
 

@@ -116,7 +116,7 @@ template <> __device__ __forceinline__ const CellF* recs_of<CellF>(const TraceAr
 // phase's), and so on towards the base level: no separate collapse phase is needed, because
 // the deepest-first schedule does not reuse a level's slots before everything below it has
 // finished. Warp-uniform.
-template <class Cell>
+template <class Cell, bool kCut>
 __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* cursor,
                             unsigned long long begin, unsigned long long end, Tally& T, DLacc& D)
 {
@@ -143,7 +143,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
     df own = {0.f, 0.f};   // own weighted sum (pass 1), kept for dL in pass 2
     float total = 0.f;     // own + descendants (pass 2), passed to the parent
     df rem = {0.f, 0.f};   // weighted sum over what follows the current segment (pass 2)
-    df rmax = LV.rmax;     // split radius of level lv
+    df rmax = LV.rmax;     // radius where the ray of level lv ends (split or cutoff)
     bool splits = false;
     unsigned ncross = 0, nrays = 0;
 
@@ -157,10 +157,14 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
             const RayBuf Pl = A.buf[lv - 1];
             const unsigned par = __ldcg(Bl.parent + slot);
             if (total != 0.f) red_f32(Pl.sub + par, total);
-            __threadfence();
-            if (atomicSub(Pl.pending + par, 1u) != 1u) { mode = 0; return; }
+            // count the parent down with acquire-release ordering: this ray's sum (above) is
+            // released with the decrement, and the lane that takes the count to zero acquires
+            // every sibling's sum before reading the parent's total
+            unsigned old;
+            asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+                         : "=r"(old) : "l"(Pl.pending + par), "r"(0xffffffffu) : "memory");
+            if (old != 1u) { mode = 0; return; }
             // last child: this lane replays the parent (pass 2)
-            __threadfence();
             lv -= 1;
             slot = par;
             const float2 ov = __ldcg(Pl.own + slot);
@@ -168,8 +172,9 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
             rem = df_add(own, {__ldcg(Pl.sub + slot), 0.f});
             total = rem.hi + rem.lo;
             const LevelInfo Lp = A.levels[lv];
-            rmax = Lp.rmax;
+            if constexpr (!kCut) rmax = Lp.rmax;
             ray_begin(A, Lp, Pl, lv, slot, W, recs, s, p, L0, splits);
+            if constexpr (kCut) rmax = end_radius(splits, Lp.rmax, A.dmax);
             Ls = __ldg(A.srcL + s);
             mode = 2;
             return;
@@ -178,7 +183,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
 
     for (;;) {
         unsigned need = __ballot_sync(kFull, mode == 0);
-        if (__popc(need) >= 8 || need == kFull) {
+        if (__popc(need) >= 12 || need == kFull) {  // measured: 12 > 8 > 4
             while (need && more) {
                 if (wnext >= wend) {
                     unsigned long long b = 0;
@@ -193,8 +198,9 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
                 if (mode == 0 && rank < avail) {
                     slot = wnext + rank;
                     lv = l;
-                    rmax = LV.rmax;
+                    if constexpr (!kCut) rmax = LV.rmax;
                     const int st = ray_begin(A, LV, B, l, slot, W, recs, s, p, L0, splits);
+                    if constexpr (kCut) rmax = end_radius(splits, LV.rmax, A.dmax);
                     if (st > 0) {
                         Ls = __ldg(A.srcL + s);
                         mode = 1;
@@ -228,7 +234,8 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
                 const float wv = cm.z;   // weight and neutral-H opacity of this cell
                 const float hv = cm.y;
                 const float q = force_weight(W.cell, W.n, A.fscale);
-                const StepOut o = walk_step<false>(W, splits, rmax, sy, sz, recs, A.tau_max);
+                // a ray ends at a radius (rmax) when it can split or (kCut) at the cutoff
+                const StepOut o = walk_step<false>(W, kCut || splits, rmax, sy, sz, recs, A.tau_max);
                 // this segment's loss: w k G, plus q dL with a force term
                 const float g = fmaf(q, o.dL, wv * gs * o.G);
                 if (mode == 1) {
@@ -247,7 +254,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
                 if (o.ev != EV_NONE) {
                     if (mode == 1) {
                         const unsigned long long c4 = 4ull * (slot - b32);
-                        if (o.ev == EV_SPLIT) {
+                        if (o.ev == EV_SPLIT && (!kCut || splits_at_end(splits, LV.rmax, A.dmax))) {
                             B.own[slot] = make_float2(own.hi, own.lo);
                             B.sub[slot] = 0.f;
                             B.pending[slot] = 4u;
@@ -266,7 +273,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
                             }
                             mode = 0;
                         } else {
-                            if (o.ev == EV_EXIT) atomicAdd(&T.escaped, (double)W.L);
+                            if (o.ev != EV_DROP) atomicAdd(&T.escaped, (double)W.L);  // exit or cut
                             else atomicAdd(&T.dropped, (double)W.L);
                             atomicAdd(&T.destroy, LV.destroy_w);
                             if (has_next) write_holes(C, c4);
@@ -287,7 +294,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
     count_rays(A.stats, l, nrays);
 }
 
-template <class Cell>
+template <class Cell, bool kCut>
 __global__ void __launch_bounds__(256, 4) k_backward_persistent(const __grid_constant__ TraceArgs A)
 {
     tally_init();
@@ -329,7 +336,7 @@ __global__ void __launch_bounds__(256, 4) k_backward_persistent(const __grid_con
         __syncthreads();
         const int l = s_level;
         if (l < 0) break;
-        run_adjoint<Cell>(A, l, &sc->cursor[l], s_begin, s_end, T, D);
+        run_adjoint<Cell, kCut>(A, l, &sc->cursor[l], s_begin, s_end, T, D);
     }
     if (D.src != 0xffffffffu && D.v.hi != 0.f) atomicAdd(A.dL + D.src, (double)D.v.hi + (double)D.v.lo);
     tally_flush(A.stats);
@@ -448,7 +455,10 @@ extern "C" int art_trace_backward(art_grid* g, const art_params* p, const float*
     A.fscale = (float)(1.0 / dV);
     // the reverse sweep is compiled for blocks of at most 256 threads (register budget)
     const int threads = p->block_threads > 0 && p->block_threads < 256 ? p->block_threads : 256;
-    void (*kern)(TraceArgs) = d_v ? k_backward_persistent<CellF> : k_backward_persistent<float4>;
+    const bool cut = p->d_max > 0.0;
+    void (*kern)(TraceArgs) =
+        d_v ? (cut ? k_backward_persistent<CellF, true> : k_backward_persistent<CellF, false>)
+            : (cut ? k_backward_persistent<float4, true> : k_backward_persistent<float4, false>);
     int per_sm = 0;
     if ((rc = status_of(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0))))
         return rc;

@@ -93,6 +93,7 @@ int check_params(const art_params* p)
     if (p->queue_capacity != 0 && (p->queue_capacity < 4 || p->queue_capacity > (1ll << 30)))
         return ART_EINVAL;
     if (p->blocks_per_sm < 0) return ART_EINVAL;
+    if (p->d_max != p->d_max || (p->d_max > 0.0 && !std::isfinite(p->d_max))) return ART_EINVAL;
     if (p->flags & ART_F_ROTATE)
         for (int i = 0; i < 9; ++i)
             if (!std::isfinite(p->rot[i])) return ART_EINVAL;
@@ -289,6 +290,8 @@ TraceArgs make_args(art_grid* g, const art_params* p)
 {
     TraceArgs A;
     std::memset(&A, 0, sizeof(A));
+    // the d_max cutoff in cell units (read only by the kernels built for a cutoff)
+    split_df(p->d_max > 0.0 ? p->d_max / g->dx : (double)kBig, A.dmax.hi, A.dmax.lo);
     A.nx = g->n[0];
     A.ny = g->n[1];
     A.nz = g->n[2];
@@ -476,7 +479,9 @@ int art_trace(art_grid* g, const art_params* p, float* d_gamma, float* d_force, 
     TraceArgs A = make_args(g, p);
     if (p->schedule == ART_SCHED_PLAIN) {
         int per_sm = 0;
-        auto kern = g->two_bin ? k_trace_level<float2> : k_trace_level<float>;
+        const bool cut = p->d_max > 0.0;
+        auto kern = g->two_bin ? (cut ? k_trace_level<float2, true> : k_trace_level<float2, false>)
+                               : (cut ? k_trace_level<float, true> : k_trace_level<float, false>);
         ART_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
         if (per_sm < 1) return ART_EINVAL;
         const int grid = per_sm * g->sms;
@@ -494,7 +499,10 @@ int art_trace(art_grid* g, const art_params* p, float* d_gamma, float* d_force, 
                                                                      &g->d_sched->count[l0]);
         ART_TRY(cudaGetLastError());
         int per_sm = 0;
-        auto kern = g->two_bin ? k_trace_persistent<float2> : k_trace_persistent<float>;
+        const bool cut = p->d_max > 0.0;
+        auto kern = g->two_bin
+                        ? (cut ? k_trace_persistent<float2, true> : k_trace_persistent<float2, false>)
+                        : (cut ? k_trace_persistent<float, true> : k_trace_persistent<float, false>);
         ART_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
         if (per_sm < 1) return ART_EINVAL;
         if (p->blocks_per_sm > 0 && p->blocks_per_sm < per_sm) per_sm = p->blocks_per_sm;

@@ -160,6 +160,7 @@ struct TraceArgs {
     float gscale;            // adjoint: sigma_H * dx / dV (gamma per unit G)
     const float* srcL;       // adjoint: source luminosities (gradients scale with them)
     const CellF* recf;       // adjoint with a force term: per cell {chi, chi_H, w, 0}, {v, 0}
+    df dmax;                 // d_max cutoff in cell units (kernels built for a cutoff only)
     float fscale;            // adjoint: force per unit momentum (1 / dV)
 };
 
@@ -470,6 +471,17 @@ __device__ __forceinline__ void tally_flush(DevStats* st)
 // Slot value of a ray buffer entry that holds no ray: the children slots of a parent that
 // did not split (each parent owns four consecutive child slots, so fronts keep pixel order).
 constexpr unsigned kHole = 0xffffffffu;
+
+// With a d_max cutoff: where a ray of a level with split radius rmax ends, and whether it
+// splits there. A ray that can split ends at min(rmax, d_max); at equal radii the cut wins.
+__device__ __forceinline__ df end_radius(bool splits, df rmax, df dmax)
+{
+    return (splits && !df_le(dmax, rmax)) ? rmax : dmax;
+}
+__device__ __forceinline__ bool splits_at_end(bool splits, df rmax, df dmax)
+{
+    return splits && !df_le(dmax, rmax);
+}
 
 // Starts the walk of ray i of level l: loads its record, its source and its direction
 // entry. Returns 1 if the ray starts inside the grid, 0 if it starts outside (it escapes at

@@ -168,3 +168,24 @@ def test_autograd_function_with_force(art):
     assert err <= PA.REL
     assert np.abs(Lt.grad.numpy() - rdL).max() <= PA.REL * np.abs(rdL).max()
     g.close()
+
+
+def test_adjoint_with_dmax_cutoff(art):
+    n = 48
+    rho = synth.lognormal_field(n, 1.5, seed=19).astype(np.float32)
+    pos = synth.uniform_positions(3, seed=19)
+    L = synth.power_law_luminosities(3, seed=19)
+    w = synth.uniform_weights(n, seed=19).astype(np.float32)
+    p = art.Params(level0=3, tau_max=30.0, sigma_H=10.0, d_max=0.37)
+    dev = torch.device("cuda")
+    g = art.Grid(torch.from_numpy(rho).to(dev), 1.0 / n)
+    g.add_sources(pos, L)
+    fwd = g.trace(p, force=False)
+    grad, dL, st = g.trace_backward(p, torch.from_numpy(w).to(dev))
+    assert st["status"] == 0 and st["crossings"] == fwd["stats"]["crossings"]
+    prob = O.Problem(nH0=rho, pos=pos, L=L, dx=1.0 / n, sigma_H=10.0, level0=3, tau_max=30.0,
+                     d_max=0.37)
+    rg, rdL, rloss = O.trace_adjoint(prob, w, nthreads=8)
+    PA.compare_field(grad.cpu().numpy(), rg, what="dloss/dlog nH0 with d_max")
+    np.testing.assert_allclose(dL.cpu().numpy(), rdL, rtol=PA.REL)
+    g.close()

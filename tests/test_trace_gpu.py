@@ -37,7 +37,7 @@ def _run(A, nH0, pos, L, dx, params, nH=None, lo=(0.0, 0.0, 0.0)):
 def _oracle(nH0, pos, L, dx, p, nH=None, threads=8):
     prob = O.Problem(nH0=nH0, pos=pos, L=L, dx=dx, nH=nH, sigma_H=p.sigma_H,
                      sigma_d=p.sigma_d, level0=p.level0, level_cap=p.level_max, m_ray=p.m_ray,
-                     tau_max=p.tau_max, rot=p.rot)
+                     tau_max=p.tau_max, rot=p.rot, d_max=p.d_max)
     return O.trace(prob, nthreads=threads)
 
 
@@ -277,3 +277,43 @@ def test_sources_added_and_fields_updated_between_traces(art):
                             level0=2, tau_max=30.0), nthreads=8)
     _check(res, ref, 0.5 * rho, p, exact_counts=ref.near_tie_rays == 0)
     g.close()
+
+
+@pytest.mark.parametrize("schedule", ["persistent", "plain"])
+def test_dmax_cutoff_64(art, schedule):
+    """Rays terminated at d_max from their source (Sec. 3.1), lognormal field with dust."""
+    n = 64
+    rho = synth.lognormal_field(n, 1.5, seed=17).astype(np.float32)
+    nH = (1.4 * rho).astype(np.float32)
+    pos = synth.uniform_positions(4, seed=17)
+    L = synth.power_law_luminosities(4, seed=17)
+    p = art.Params(level0=3, tau_max=30.0, sigma_H=6.0, sigma_d=1.0, schedule=schedule,
+                   d_max=0.31)
+    res = _run(art, rho, pos, L, 1.0 / n, p, nH=nH)
+    ref = _oracle(rho, pos, L, 1.0 / n, p, nH=nH)
+    _check(res, ref, rho, p, nH=nH)
+    assert res["stats"]["L_escaped"] == pytest.approx(ref.escaped, rel=1e-5)
+    # cells beyond d_max (plus a cell diagonal) of every source stay empty
+    k, j, i = np.indices((n, n, n))
+    c = (np.stack([i, j, k], -1) + 0.5) / n
+    far = np.all([np.linalg.norm(c - q, axis=-1) > 0.31 + math.sqrt(3) / n for q in pos], axis=0)
+    assert far.any() and np.all(res["gamma"][far] == 0.0)
+
+
+def test_dmax_at_a_split_radius_and_without_effect(art):
+    """d_max exactly at r_max(l) cuts (no level l+1 rays); d_max beyond the box is a no-op."""
+    n = 32
+    pos = [[0.5 + 0.2 / n, 0.5 + 0.3 / n, 0.5 - 0.1 / n]]
+    rho = np.full((n, n, n), 0.5, dtype=np.float32)
+    r3 = math.sqrt(3.0 / (math.pi * 4.0)) * 2**3 / n
+    p = art.Params(level0=2, tau_max=30.0, sigma_H=2.0, d_max=r3)
+    res = _run(art, rho, pos, [1.0], 1.0 / n, p)
+    ref = _oracle(rho, pos, [1.0], 1.0 / n, p)
+    assert res["stats"]["rays_per_level"][2:5] == [192, 768, 0] == ref.rays_per_level[2:5].tolist()
+    _check(res, ref, rho, p)
+    p_far = art.Params(level0=2, tau_max=30.0, sigma_H=2.0, d_max=5.0)
+    p_none = art.Params(level0=2, tau_max=30.0, sigma_H=2.0)
+    a = _run(art, rho, pos, [1.0], 1.0 / n, p_far)
+    b = _run(art, rho, pos, [1.0], 1.0 / n, p_none)
+    assert a["stats"]["crossings"] == b["stats"]["crossings"]
+    PA.compare_field(a["gamma"], b["gamma"], rel=1e-6, what="gamma, d_max beyond the box")
