@@ -182,16 +182,19 @@ def test_integer_tallies_deterministic(art):
     np.testing.assert_allclose(a["gamma"], b["gamma"], rtol=1e-5, atol=1e-6 * a["gamma"].max())
 
 
-@pytest.mark.parametrize("schedule", ["persistent", "plain"])
-def test_two_bin_dust_radiation_pressure(art, schedule):
-    """Second, non-ionizing bin (Sec. 2.3): dust-only attenuation, force of both bins."""
+@pytest.mark.parametrize("schedule,d_max", [("persistent", 0.0), ("plain", 0.0),
+                                             ("persistent", 0.28)])
+def test_two_bin_dust_radiation_pressure(art, schedule, d_max):
+    """Second, non-ionizing bin (Sec. 2.3): dust-only attenuation, force of both bins; also
+    with the d_max cutoff (both bins end there)."""
     n = 48
     rho = synth.lognormal_field(n, 1.5, seed=11)
     pos = synth.uniform_positions(4, seed=11)
     L = synth.power_law_luminosities(4, seed=11)
     Ln = 3.0 * synth.power_law_luminosities(4, seed=12)
     nH0, nH = 0.3 * rho, rho
-    p = art.Params(level0=3, tau_max=30.0, sigma_H=20.0, sigma_d=6.0, schedule=schedule)
+    p = art.Params(level0=3, tau_max=30.0, sigma_H=20.0, sigma_d=6.0, schedule=schedule,
+                   d_max=d_max)
     dev = torch.device("cuda")
     g = art.Grid(torch.as_tensor(nH0.astype(np.float32), device=dev), 1.0 / n,
                  nH=torch.as_tensor(nH.astype(np.float32), device=dev))
@@ -200,7 +203,7 @@ def test_two_bin_dust_radiation_pressure(art, schedule):
     out = g.trace(p, force=True, energy=True)
     res = {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in out.items()}
     prob = O.Problem(nH0=nH0, pos=pos, L=L, dx=1.0 / n, nH=nH, sigma_H=20.0, sigma_d=6.0,
-                     level0=3, tau_max=30.0, Ln=Ln)
+                     level0=3, tau_max=30.0, Ln=Ln, d_max=d_max)
     ref = O.trace(prob, nthreads=8)
     st = res["stats"]
     assert st["status"] == 0 and st["destroy"] == st["destroy_expected"]
