@@ -34,26 +34,6 @@ using namespace art;
 namespace {
 
 
-// d/dx of (1 - e^-x)/x. Taylor series below 1 (no cancellation), closed form above.
-__device__ __forceinline__ float dphi_of(float x, float em)
-{
-    if (x < 1.f) {
-        float r = 1.f / 518918400.f;
-        r = fmaf(r, x, -1.f / 43545600.f);
-        r = fmaf(r, x, 1.f / 3991680.f);
-        r = fmaf(r, x, -1.f / 403200.f);
-        r = fmaf(r, x, 1.f / 45360.f);
-        r = fmaf(r, x, -1.f / 5760.f);
-        r = fmaf(r, x, 1.f / 840.f);
-        r = fmaf(r, x, -1.f / 144.f);
-        r = fmaf(r, x, 1.f / 30.f);
-        r = fmaf(r, x, -1.f / 8.f);
-        r = fmaf(r, x, 1.f / 3.f);
-        return fmaf(r, x, -0.5f);
-    }
-    return ((1.f + x) * (1.f + em) - 1.f) / (x * x);
-}
-
 // Running sum in two floats without renormalisation: hi + g is split exactly (two-sum) and
 // its rounding error collected in lo.
 __device__ __forceinline__ df df_acc(df a, float g)
@@ -128,7 +108,6 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
     const RayBuf C = A.buf[l + 1];
     const bool has_next = l < A.lmax_glob;
     const float gs = A.gscale;
-    const int sy = A.nx, sz = A.nx * A.ny;
 
     // slot indices fit in 32 bits (level buffers hold fewer than 2^31 slots)
     const unsigned b32 = (unsigned)begin, e32 = (unsigned)end;
@@ -235,7 +214,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
                 const float hv = cm.y;
                 const float q = force_weight(W.cell, W.n, A.fscale);
                 // a ray ends at a radius (rmax) when it can split or (kCut) at the cutoff
-                const StepOut o = walk_step<false>(W, kCut || splits, rmax, sy, sz, recs, A.tau_max);
+                const StepOut o = walk_step<false, true>(W, kCut || splits, rmax, recs, A.tau_max);
                 // this segment's loss: w k G, plus q dL with a force term
                 const float g = fmaf(q, o.dL, wv * gs * o.G);
                 if (mode == 1) {
@@ -244,10 +223,9 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
                 } else {
                     rem = df_dec(rem, g);
                     const float after = rem.hi + rem.lo;
-                    const float dphi = dphi_of(o.dtau, -o.dtau * o.phi);
                     // d(segment loss)/d dtau: w k L_in ds phi' + q L_in e^-dtau (W.L is now
                     // L_in e^-dtau)
-                    const float own_d = fmaf(q, W.L, wv * gs * o.Lin * o.ds * dphi);
+                    const float own_d = fmaf(q, W.L, wv * gs * o.Lin * o.ds * o.dphi);
                     const float val = Ls * hv * o.ds * (own_d - after);
                     if (o.cell >= 0) red_f32(A.grad + o.cell, val);
                 }
@@ -443,7 +421,6 @@ extern "C" int art_trace_backward(art_grid* g, const art_params* p, const float*
     }
     if ((rc = status_of(cudaGetLastError()))) return rc;
     TraceArgs A = make_args(g, p);
-    if (p->chunk == 0) A.chunk = 32;  // measured best for the reverse sweep (64 for the forward)
     A.rec = g->d_rec;
     A.recf = d_v ? g->d_recf : nullptr;
     A.w = d_w;

@@ -203,6 +203,7 @@ struct WalkT {
     df tc;        // distance of the current position
     int idx;      // linear index of the current cell
     int rem[3];   // cells left on each axis before the ray leaves the grid
+    int ss[3];    // signed index step of a crossing on each axis
     float n[3];   // direction (hi parts) for momentum deposits
     float L, tau;
     float Ln, taun;  // non-ionizing bin (two-bin traces only)
@@ -232,11 +233,14 @@ __device__ __forceinline__ bool walk_start(WalkT<Cell>& W, int nx, int ny, int n
         if (n[a].hi != 0.f) {
             const bool up = n[a].hi > 0.f;
             W.rem[a] = up ? N[a] - 1 - ci : ci;
+            const int stride = a == 0 ? 1 : (a == 1 ? nx : nx * ny);
+            W.ss[a] = up ? stride : -stride;
             const df off = df_add({(float)(up ? ci + 1 : ci), 0.f}, df_neg(u[a]));
             W.t[a] = df_mul(off, inv[a]);
             W.d[a] = up ? inv[a] : df_neg(inv[a]);
         } else {
             W.rem[a] = 1 << 30;
+            W.ss[a] = 0;
             W.t[a] = {kBig, 0.f};
             W.d[a] = {0.f, 0.f};
         }
@@ -255,6 +259,7 @@ struct StepOut {
     float G;      // L_in ds phi(dtau)
     float dL;     // L_in (1 - e^-dtau)
     float phi;    // (1 - e^-dtau)/dtau
+    float dphi;   // d phi / d dtau (filled by walk_step<kCountOnly, true> only)
     float dLn;    // two-bin traces: loss of the non-ionizing bin (chi_n = n_H sigma_d)
     int ev;
 };
@@ -277,14 +282,38 @@ __device__ __forceinline__ float phi_of(float x)
     return x < 1.f ? small : large;
 }
 
+// phi(x) and phi'(x) from the same exponential (the reverse sweep needs both). Below 1, with
+// y = x/2, E = e^{-y} and S = sinh(y)/y: phi = E S and phi' = E (S'(y) - S) / 2, S' to y^7
+// (S' - S stays near -1, so nothing cancels); above 1, phi' = (e^{-x} - phi)/x.
+__device__ __forceinline__ float phi_dphi(float x, float& dphi)
+{
+    const float y = 0.5f * x;
+    const float E = __expf(-y);
+    const float y2 = y * y;
+    float S = fmaf(y2, 1.f / 362880.f, 1.f / 5040.f);
+    S = fmaf(S, y2, 1.f / 120.f);
+    S = fmaf(S, y2, 1.f / 6.f);
+    S = fmaf(S, y2, 1.f);
+    float Sp = fmaf(y2, 1.f / 45360.f, 1.f / 840.f);
+    Sp = fmaf(Sp, y2, 1.f / 30.f);
+    Sp = fmaf(Sp, y2, 1.f / 3.f);
+    Sp *= y;
+    const float r = __fdividef(1.f, fmaxf(x, 1.f));
+    const float E2 = E * E;
+    const float large = (1.f - E2) * r;
+    const bool sm = x < 1.f;
+    dphi = sm ? 0.5f * E * (Sp - S) : (E2 - large) * r;
+    return sm ? E * S : large;
+}
+
 __device__ __forceinline__ df df_sel(bool c, df a, df b) { return {c ? a.hi : b.hi, c ? a.lo : b.lo}; }
 
 // One step of the walk: the segment from tc to the next face or to the split radius rmax
 // (when the ray splits at all). The common case (one axis crossing) runs without branches;
 // faces crossed together (ties) take a short side path. When the step ends the ray (event
 // other than EV_NONE) the walk state other than L and tau is left unspecified.
-template <bool kCountOnly, class Cell>
-__device__ __forceinline__ StepOut walk_step(WalkT<Cell>& W, bool splits, df rmax, int sy, int sz,
+template <bool kCountOnly, bool kDphi = false, class Cell>
+__device__ __forceinline__ StepOut walk_step(WalkT<Cell>& W, bool splits, df rmax,
                                              const Cell* __restrict__ cells, float tau_max)
 {
     StepOut o;
@@ -302,9 +331,7 @@ __device__ __forceinline__ StepOut walk_step(WalkT<Cell>& W, bool splits, df rma
     bool split = splits && rmax.hi < hm;
     bool m0 = a == 0, m1 = a == 1, m2 = a == 2;
     // next cell and whether it leaves the grid, for the usual single-axis crossing
-    const float na = a == 0 ? W.n[0] : (a == 1 ? W.n[1] : W.n[2]);
-    const int st = a == 0 ? 1 : (a == 1 ? sy : sz);
-    int nidx = W.idx + (na > 0.f ? st : -st);
+    int nidx = W.idx + (a == 0 ? W.ss[0] : (a == 1 ? W.ss[1] : W.ss[2]));
     bool out = (a == 0 ? W.rem[0] : (a == 1 ? W.rem[1] : W.rem[2])) == 0;
     if (h0 == h1 || h0 == h2 || h1 == h2 || (splits && rmax.hi == hm)) {
         const bool e01 = df_le(W.t[0], W.t[1]);
@@ -320,8 +347,7 @@ __device__ __forceinline__ StepOut walk_step(WalkT<Cell>& W, bool splits, df rma
         m0 = df_diff(W.t[0], tm) <= tol;
         m1 = df_diff(W.t[1], tm) <= tol;
         m2 = df_diff(W.t[2], tm) <= tol;
-        nidx = W.idx + (m0 ? (W.n[0] > 0.f ? 1 : -1) : 0) + (m1 ? (W.n[1] > 0.f ? sy : -sy) : 0) +
-               (m2 ? (W.n[2] > 0.f ? sz : -sz) : 0);
+        nidx = W.idx + (m0 ? W.ss[0] : 0) + (m1 ? W.ss[1] : 0) + (m2 ? W.ss[2] : 0);
         out = (m0 && W.rem[0] == 0) || (m1 && W.rem[1] == 0) || (m2 && W.rem[2] == 0);
         // tied axes other than a advance here; axis a advances with the common path below
         if (m0 && a != 0) W.t[0] = df_add(W.t[0], W.d[0]);
@@ -339,7 +365,9 @@ __device__ __forceinline__ StepOut walk_step(WalkT<Cell>& W, bool splits, df rma
     o.Lin = W.L;
     o.dtau = x;
     if (!kCountOnly) {
-        const float ph = phi_of(x);
+        float ph;
+        if constexpr (kDphi) ph = phi_dphi(x, o.dphi);
+        else ph = phi_of(x);
         o.phi = ph;
         o.G = W.L * ds * ph;
         o.dL = W.L * x * ph;
