@@ -170,11 +170,12 @@ def run_ours(args, rank, world, local_rank):
         grid = A.Grid(nH0, 1.0 / n, stream=stream)
         grid.add_sources(pos, L)
     gamma = torch.empty_like(nH)
+    force = torch.empty((3,) + tuple(nH.shape), device=dev, dtype=torch.float32)
     alpha = cfg["alpha"]
     dt = 0.1 / (alpha * cfg["nbar"]) if alpha else 0.0
 
     def enqueue_step():
-        grid.trace(p, force=False, stats=False, out={"gamma": gamma})
+        grid.trace(p, force=True, stats=False, out={"gamma": gamma, "force": force})
         if alpha:
             A.xn_update(gamma, nH, xn, alpha, dt, nH0_out=nH0, stream=stream)
 
@@ -422,7 +423,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     cfg = CONFIGS[args.config]
     config = {"workload": f"{cfg['n']}^3 lognormal sigma_ln={cfg['sigma_ln']}, {cfg['nsrc']} "
-                          f"power-law sources, l0=4, m_ray=4, tau_max=30"
+                          f"power-law sources, l0=4, m_ray=4, tau_max=30, gamma and force"
                           + (", trace + Eq. e:xn3 update per step" if cfg["alpha"] else ""),
               "grid": cfg["n"], "sources": cfg["nsrc"], "schedule": args.schedule,
               "cuda_graph": args.graph,
