@@ -165,9 +165,10 @@ __device__ void run_rays(const TraceArgs& A, const Cell* cells, int l,
     constexpr bool two = TwoBin<Cell>::value;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt = (1u << lane) - 1u;
-    const LevelInfo LV = A.levels[l];
-    const RayBuf B = A.buf[l];
-    const RayBuf C = A.buf[l + 1];
+    const LevelInfo& LV = A.levels[l];
+    const df lv_rmax = LV.rmax;  // split radius of this level, kept in registers
+    const RayBuf& B = A.buf[l];
+    const RayBuf& C = A.buf[l + 1];
     const bool has_next = l < A.lmax_glob;
 
     // slot indices fit in 32 bits (level buffers hold fewer than 2^31 slots)
@@ -233,10 +234,10 @@ __device__ void run_rays(const TraceArgs& A, const Cell* cells, int l,
                 // a ray ends at a radius when it can split or (kCut) at the d_max cutoff
                 StepOut o;
                 if constexpr (kCut)
-                    o = walk_step<false>(W, true, end_radius(splits, LV.rmax, A.dmax), cells,
+                    o = walk_step<false>(W, true, end_radius(splits, lv_rmax, A.dmax), cells,
                                          A.tau_max);
                 else
-                    o = walk_step<false>(W, splits, LV.rmax, cells, A.tau_max);
+                    o = walk_step<false>(W, splits, lv_rmax, cells, A.tau_max);
                 cell = o.cell;  // < 0 when the segment had no length
                 const float dm = two ? o.dL + o.dLn : o.dL;  // momentum of both bins
                 dv = make_float4(o.G, dm * W.n[0], dm * W.n[1], dm * W.n[2]);
