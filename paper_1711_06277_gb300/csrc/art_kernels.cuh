@@ -227,7 +227,7 @@ __device__ void run_rays(const TraceArgs& A, const Cell* cells, int l,
         }
 
 #pragma unroll 1
-        for (int k = 0; k < 16; ++k) {  // steps between refill checks (measured: 16 > 8 > 4 > 2)
+        for (int k = 0; k < 32; ++k) {  // steps between refill checks (measured: 32 > 16 > 8 > 4)
             int cell = -1;
             float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
             if (active) {
