@@ -25,7 +25,7 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tune
 DEFAULT_SPACE = {
     "chunk": [32, 64, 128],
     "block_threads": [128, 256, 512],
-    "queue_capacity": [16 << 20, 64 << 20],
+    "queue_capacity": [16 << 20, 64 << 20, 256 << 20],  # rays per deep-level buffer (16 B each)
 }
 
 
