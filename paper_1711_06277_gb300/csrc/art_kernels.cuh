@@ -150,7 +150,7 @@ __global__ void k_inject(int s0, int nsrc, unsigned npix0, RayBuf B, unsigned lo
 // `begin` (cursor advanced atomically by warps, `chunk` slots at a time). The children of
 // the ray in slot i go to slots 4 (i - begin) .. +3 of level l + 1, so the next front keeps
 // the pixel order of this one; parents that do not split mark their four slots empty. Idle
-// lanes are refilled once 14 of the 32 are idle, so the ray set-up runs with many lanes at
+// lanes are refilled once 16 of the 32 are idle, so the ray set-up runs with many lanes at
 // once. Warp-uniform: every lane of the warp must call it.
 // The per-cell records a trace gathers: opacities (one bin) or opacity pairs (two bins).
 template <class Cell> __device__ __forceinline__ const Cell* cells_of(const TraceArgs& A);
@@ -188,7 +188,7 @@ __device__ void run_rays(const TraceArgs& A, const Cell* cells, int l,
     for (;;) {
         // refill idle lanes from the warp's chunk, fetching chunks as needed
         unsigned need = __ballot_sync(kFull, !active);
-        if (__popc(need) >= 14 || need == kFull) {  // measured: 14 > 12 > 10, 8 > 4
+        if (__popc(need) >= 16 || need == kFull) {  // measured: 16 > 18, 14 > 12 > 10
             while (need && more) {
                 if (wnext >= wend) {
                     unsigned long long b = 0;
@@ -227,7 +227,7 @@ __device__ void run_rays(const TraceArgs& A, const Cell* cells, int l,
         }
 
 #pragma unroll 1
-        for (int k = 0; k < 32; ++k) {  // steps between refill checks (measured: 32 > 16 > 8 > 4)
+        for (int k = 0; k < 64; ++k) {  // steps between refill checks (measured: 64 > 32 > 16 > 8)
             int cell = -1;
             float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
             if (active) {
