@@ -23,7 +23,7 @@ from . import art as A
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tune_cache.json")
 
 DEFAULT_SPACE = {
-    "chunk": [32, 64, 128],
+    "chunk": [32, 64, 96, 128],
     "block_threads": [128, 256, 512],
     "queue_capacity": [16 << 20, 64 << 20, 256 << 20],  # rays per deep-level buffer (16 B each)
 }
