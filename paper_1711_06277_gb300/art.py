@@ -8,7 +8,7 @@ grid's device; the library borrows them for the duration noted in ``include/art.
 from __future__ import annotations
 
 import ctypes
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 import torch

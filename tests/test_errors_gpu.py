@@ -1,6 +1,5 @@
 """Failure detection without a GPU fault: bounded waits that give up, ray-front overflow,
 bad inputs and calls out of order all come back as status codes."""
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
