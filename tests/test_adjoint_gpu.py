@@ -189,3 +189,32 @@ def test_adjoint_with_dmax_cutoff(art):
     PA.compare_field(grad.cpu().numpy(), rg, what="dloss/dlog nH0 with d_max")
     np.testing.assert_allclose(dL.cpu().numpy(), rdL, rtol=PA.REL)
     g.close()
+
+
+def test_adjoint_with_rotation_and_plain_schedule_request(art):
+    """Rotated ray directions (the same tables as the forward trace) and a plain-schedule
+    request: the reverse sweep always runs its persistent schedule and must give the same
+    result."""
+    n = 40
+    rho = synth.lognormal_field(n, 1.5, seed=23).astype(np.float32)
+    pos = synth.uniform_positions(3, seed=23)
+    L = synth.power_law_luminosities(3, seed=23)
+    w = synth.uniform_weights(n, seed=23).astype(np.float32)
+    R = synth.random_rotation(23)
+    dev = torch.device("cuda")
+    g = art.Grid(torch.from_numpy(rho).to(dev), 1.0 / n)
+    g.add_sources(pos, L)
+    outs = []
+    for schedule in ("persistent", "plain"):
+        p = art.Params(level0=3, tau_max=30.0, sigma_H=9.0, rot=R, schedule=schedule)
+        g.trace(p, force=False)
+        grad, dL, st = g.trace_backward(p, torch.from_numpy(w).to(dev))
+        assert st["status"] == 0
+        outs.append((grad.cpu().numpy(), dL.cpu().numpy()))
+    g.close()
+    prob = O.Problem(nH0=rho, pos=pos, L=L, dx=1.0 / n, sigma_H=9.0, level0=3, tau_max=30.0,
+                     rot=R)
+    rg, rdL, _ = O.trace_adjoint(prob, w, nthreads=8)
+    for grad, dL in outs:
+        PA.compare_field(grad, rg, what="dloss/dlog nH0, rotated")
+        np.testing.assert_allclose(dL, rdL, rtol=PA.REL)
