@@ -71,7 +71,11 @@ typedef struct {
     int chunk;           /* rays a warp takes from the queue at a time (0 = library choice) */
     long long queue_capacity; /* rays per level buffer beyond l0 (0 = library choice) */
     double wait_limit_s; /* bound on any device-side wait (grid barrier); 0 = library default
-                            (10 s); a negative value makes every wait give up at once */
+                            (60 s); a negative value makes every wait give up at once. A
+                            block waits at a barrier while the slowest block finishes its
+                            share of one phase of the schedule, so grids and source sets
+                            whose phases run longer than the bound need a larger value
+                            (the trace then fails with ART_ETIMEOUT, results incomplete) */
     int blocks_per_sm;   /* resident blocks per SM of the persistent trace (0 = as many as
                             fit); fewer blocks keep fewer rays in flight */
     double d_max;        /* > 0: every ray ends at this distance from its source (the cutoff
@@ -100,7 +104,10 @@ typedef struct {
  * sigma_d = 0, identity rotation, persistent schedule, library-chosen launch knobs. */
 void art_params_default(art_params* p);
 
-/* Creates a grid of nx*ny*nz cells of side dx whose lower corner is box_lo[3].
+/* Creates a grid of nx*ny*nz cells of side dx whose lower corner is box_lo[3]: the uniform
+ * Cartesian grid through which rays are traced (Sec. 2.1), holding the neutral and total
+ * hydrogen densities from which the opacity chi_i = n_HI sigma_H + n_H sigma_d is formed
+ * (Sec. 2.3).
  * d_nH0: device, nx*ny*nz floats, neutral H density (required, finite, >= 0).
  * d_nH: device, total H density for the dust term, or NULL for no dust.
  * stream: a cudaStream_t (NULL = legacy default stream) on the current device; all work of
@@ -111,11 +118,15 @@ void art_params_default(art_params* p);
 int art_create_grid(art_grid** out, int nx, int ny, int nz, const double box_lo[3], double dx,
                     const float* d_nH0, const float* d_nH, void* stream);
 
-/* Re-points the density fields (same sizes and ownership rules as at creation). The fields
- * are read again by every trace, so updating their contents in place needs no call. */
+/* Re-points the density fields (same sizes and ownership rules as at creation): the n_HI
+ * (and n_H) of Sec. 2.3, which change between radiation substeps as the neutral fraction is
+ * updated (Eq. e:xn3, then n_HI = x_n n_H). The fields are read again by every trace, so
+ * updating their contents in place needs no call. Errors: ART_EINVAL (g or d_nH0 NULL). */
 int art_update_fields(art_grid* g, const float* d_nH0, const float* d_nH);
 
-/* Appends n sources. h_pos: host, n*3 doubles (x, y, z), each strictly inside the box.
+/* Appends n point sources at x_src with luminosity L (Sec. 2.1: each injects L/N_ray(l0)
+ * along every base-level HEALPix direction; several sources add their rays' deposits).
+ * h_pos: host, n*3 doubles (x, y, z), each strictly inside the box.
  * h_L: host, n doubles, luminosities >= 0 (photon rates). The arrays are copied.
  * Errors: ART_EINVAL (n < 0, a source on or outside the box boundary, negative or
  * non-finite luminosity). */
@@ -158,14 +169,18 @@ int art_trace(art_grid* g, const art_params* p, float* d_gamma, float* d_force,
  * trace). Returns the device status of that trace. ART_ESTATE if nothing was traced. */
 int art_get_stats(art_grid* g, art_stats* h_stats);
 
-/* Gradient of loss = sum_c (w_c gamma_c + v_c . force_c) for the fields and sources of the
- * last call (new; the paper has no adjoint): recomputes every ray's path in reverse level
- * order instead of storing segments, summing child-ray adjoints into their parents.
+/* Gradient of loss = sum_c (w_c gamma_c + v_c . force_c) for the current fields and sources
+ * (new; the paper has no adjoint; the forward map is the trace of Sec. 2.1 with the opacity
+ * of Sec. 2.3): recomputes every ray's path in reverse level order instead of storing
+ * segments, summing child-ray adjoints into their parents.
  *   d_w:          device, ncell floats, dloss/dgamma per cell, or NULL (no gamma term);
  *   d_v:          device, 3*ncell floats (SoA blocks x, y, z, like art_trace's d_force),
  *                 dloss/dforce per cell, or NULL (no force term); not both NULL;
  *   d_dlog_nH0:   device, ncell floats, output dloss/dlog(n_H0) per cell (overwritten);
  *   d_dL:         device, n_src doubles, output dloss/dL per source (overwritten), or NULL.
+ *                 Device memory (not host) so that the call never synchronizes and can sit
+ *                 in a CUDA graph or in a torch autograd backward without a host round trip;
+ *                 callers copy the n_src doubles out when they need them.
  * Split points and tau_max retirement are held fixed. A force term doubles the per-step
  * gather (32-byte cell records, 32 B x ncell of library memory). One-bin traces only
  * (ART_EINVAL with a second bin). Same parameters and status rules as art_trace; h_stats
@@ -204,8 +219,10 @@ long long art_dt_scratch_bytes(long long ncell);
  *   - ncell must be in 1..ART_DT_STATIC_MAX_CELLS (2^24); larger inputs return ART_EINVAL
  *     with nothing enqueued;
  *   - the first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call before any
- *     stream capture;
+ *     (cudaGetSymbolAddress) with that device current and keeps it for the life of the
+ *     process; make that first call before any stream capture. The kept address belongs to
+ *     the device's primary context: after cudaDeviceReset on a device this entry point must
+ *     not be called on that device again;
  *   - every call on a device shares the one array, which keeps the last call's partials;
  *     each call writes every partial it reads, so no clearing is needed, but calls whose
  *     GPU work overlaps (different streams, no ordering between them) race and give wrong

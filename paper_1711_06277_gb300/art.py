@@ -219,19 +219,26 @@ class ARTFunction(torch.autograd.Function):
     hand-written adjoint in ``backward``.
 
     Inputs: log_nH0 (nz,ny,nx) float32 CUDA, L (n_src,) float64 (any device); ``grid`` is a
-    Grid whose sources sit at the positions to trace (their luminosities are replaced by L);
-    ``params`` the trace parameters. gamma and force carry gradients.
+    Grid (its total-density field, if any, is kept for the dust term); ``positions`` the
+    (n_src, 3) source positions; ``params`` the trace parameters. gamma and force carry
+    gradients. The grid is shared state: ``forward`` points it at this call's neutral
+    density and sources, and ``backward`` points it back at them before the reverse sweep,
+    so other traces of the same grid between the two calls do not change the gradient.
     """
 
     @staticmethod
     def forward(ctx, log_nH0: torch.Tensor, L: torch.Tensor, grid: Grid, params: Params,
                 positions, with_force: bool = False):
         nH0 = torch.exp(log_nH0.detach()).contiguous()
-        grid.update_fields(nH0)
+        nH = grid._nH
+        pos = np.array(positions, dtype=np.float64).reshape(-1, 3)
+        Lh = L.detach().double().cpu().numpy().copy()
+        grid.update_fields(nH0, nH)
         grid.clear_sources()
-        grid.add_sources(positions, L.detach().double().cpu().numpy())
+        grid.add_sources(pos, Lh)
         out = grid.trace(params, force=with_force, stats=False)
-        ctx.grid, ctx.params, ctx.nH0 = grid, params, nH0
+        ctx.grid, ctx.params, ctx.nH0, ctx.nH = grid, params, nH0, nH
+        ctx.pos, ctx.L = pos, Lh
         ctx.L_device = L.device
         ctx.with_force = with_force
         if with_force:
@@ -240,9 +247,11 @@ class ARTFunction(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, dgamma: torch.Tensor, dforce: torch.Tensor | None = None):
-        grid = ctx.grid
-        grid.update_fields(ctx.nH0)
         if dgamma is None and dforce is None:
             return None, None, None, None, None, None
+        grid = ctx.grid
+        grid.update_fields(ctx.nH0, ctx.nH)
+        grid.clear_sources()
+        grid.add_sources(ctx.pos, ctx.L)
         grad, dL, _ = grid.trace_backward(ctx.params, dgamma, stats=False, v=dforce)
         return grad, dL.to(ctx.L_device), None, None, None, None

@@ -14,7 +14,7 @@ using namespace art;
 
 namespace {
 
-constexpr double kDefaultWaitS = 10.0;
+constexpr double kDefaultWaitS = 60.0;
 
 int cuda_status(cudaError_t e)
 {
@@ -552,7 +552,7 @@ int art_get_stats(art_grid* g, art_stats* h_stats)
 void art_destroy_grid(art_grid* g)
 {
     if (!g) return;
-    if (g->stream || true) cudaStreamSynchronize(g->stream);
+    cudaStreamSynchronize(g->stream);
     dev_free(g->d_chi);
     dev_free(g->d_chiH);
     dev_free(g->d_acc);

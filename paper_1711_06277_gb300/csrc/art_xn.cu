@@ -142,7 +142,13 @@ int art_xn_update(void* stream, long long ncell, const float* d_gamma, const flo
     if (!(alpha_B > 0.0) || !(dt >= 0.0) || !std::isfinite(dt) || (method != 0 && method != 1))
         return ART_EINVAL;
     if (ncell == 0) return ART_OK;
-    const int blocks = (int)((ncell + 255) / 256 < 152 * 16 ? (ncell + 255) / 256 : 152 * 16);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return ART_ECUDA;
+    // a grid-stride loop over 16 resident blocks of 256 threads per SM
+    const long long cap = 16ll * (sms > 0 ? sms : 1);
+    const int blocks = (int)((ncell + 255) / 256 < cap ? (ncell + 255) / 256 : cap);
     k_xn_update<<<blocks, 256, 0, (cudaStream_t)stream>>>(ncell, d_gamma, d_nH, d_xn, d_nH0,
                                                           (float)alpha_B, (float)dt, method);
     return cudaGetLastError() == cudaSuccess ? ART_OK : ART_ECUDA;

@@ -218,3 +218,58 @@ def test_adjoint_with_rotation_and_plain_schedule_request(art):
     for grad, dL in outs:
         PA.compare_field(grad, rg, what="dloss/dlog nH0, rotated")
         np.testing.assert_allclose(dL, rdL, rtol=PA.REL)
+
+
+def test_autograd_two_forwards_then_backward(art):
+    """Two ARTFunction calls with different sources on one shared Grid, then the backward of
+    the first: the reverse sweep must trace the first call's sources and field."""
+    n = 32
+    rho = synth.lognormal_field(n, 1.5, seed=31).astype(np.float32)
+    pos_a = synth.uniform_positions(3, seed=31)
+    pos_b = synth.uniform_positions(2, seed=32)
+    L_a = synth.power_law_luminosities(3, seed=31)
+    L_b = synth.power_law_luminosities(2, seed=32)
+    w = synth.uniform_weights(n, seed=31).astype(np.float32)
+    p = art.Params(level0=3, tau_max=30.0, sigma_H=8.0)
+    g = art.Grid(torch.from_numpy(rho).cuda(), 1.0 / n)
+    logn = torch.log(torch.from_numpy(rho).cuda()).requires_grad_(True)
+    La = torch.tensor(L_a, dtype=torch.float64, requires_grad=True)
+    gamma_a = art.ARTFunction.apply(logn, La, g, p, pos_a)
+    # a second forward on the same grid with other sources and a denser field
+    logn_b = (logn.detach() + 0.7).requires_grad_(True)
+    Lb = torch.tensor(L_b, dtype=torch.float64, requires_grad=True)
+    art.ARTFunction.apply(logn_b, Lb, g, p, pos_b)
+    (gamma_a.double() * torch.from_numpy(w).cuda().double()).sum().backward()
+    prob = O.Problem(nH0=rho, pos=pos_a, L=L_a, dx=1.0 / n, sigma_H=8.0, level0=3, tau_max=30.0)
+    rg, rdL, _ = O.trace_adjoint(prob, w, nthreads=8)
+    PA.compare_field(logn.grad.cpu().numpy(), rg, rel=3e-5, what="grad after a second forward")
+    np.testing.assert_allclose(La.grad.numpy(), rdL, rtol=PA.REL)
+    g.close()
+
+
+def test_autograd_with_dust(art):
+    """A grid with a total-density field: ARTFunction keeps the dust term of the opacity
+    (chi = n_H0 sigma_H + n_H sigma_d, Sec. 2.3) in both the forward and the reverse sweep."""
+    n = 32
+    rho = synth.lognormal_field(n, 1.5, seed=33).astype(np.float32)
+    nH = (1.6 * rho).astype(np.float32)
+    pos = synth.uniform_positions(3, seed=33)
+    L = synth.power_law_luminosities(3, seed=33)
+    w = synth.uniform_weights(n, seed=33).astype(np.float32)
+    p = art.Params(level0=3, tau_max=30.0, sigma_H=8.0, sigma_d=3.0)
+    g = art.Grid(torch.from_numpy(rho).cuda(), 1.0 / n, nH=torch.from_numpy(nH).cuda())
+    logn = torch.log(torch.from_numpy(rho).cuda()).requires_grad_(True)
+    Lt = torch.tensor(L, dtype=torch.float64, requires_grad=True)
+    gamma = art.ARTFunction.apply(logn, Lt, g, p, pos)
+    prob = O.Problem(nH0=rho, pos=pos, L=L, dx=1.0 / n, nH=nH, sigma_H=8.0, sigma_d=3.0,
+                     level0=3, tau_max=30.0)
+    ref = O.trace(prob, nthreads=8)
+    PA.compare_field(gamma.detach().cpu().numpy(), ref.gamma, what="gamma with dust")
+    (gamma.double() * torch.from_numpy(w).cuda().double()).sum().backward()
+    rg, rdL, _ = O.trace_adjoint(prob, w, nthreads=8)
+    PA.compare_field(logn.grad.cpu().numpy(), rg, rel=3e-5, what="autograd grad with dust")
+    np.testing.assert_allclose(Lt.grad.numpy(), rdL, rtol=PA.REL)
+    # a plain trace of the grid afterwards still sees the dust field
+    out = g.trace(p, force=False)
+    PA.compare_field(out["gamma"].cpu().numpy(), ref.gamma, what="gamma after backward")
+    g.close()

@@ -44,9 +44,10 @@ def test_static_substep_matches_allocating_entry_point():
         pytest.skip("no GPU")
     L = C.lib()
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    # two calls in a row with different inputs and sizes: the second must not see the
-    # first call's partials
-    for n, seed, alpha, Cc in [(3_000_001, 1, 0.05, 0.1), (777, 2, 0.2, 0.3)]:
+    # calls in a row with different inputs and sizes: a later call must not see an earlier
+    # call's partials. The largest size fills the fixed array exactly (65,536 tiles).
+    for n, seed, alpha, Cc in [(3_000_001, 1, 0.05, 0.1), (777, 2, 0.2, 0.3),
+                               (C.ART_DT_STATIC_MAX_CELLS, 3, 0.1, 0.1), (1000, 4, 0.05, 0.1)]:
         gam, nH, xn = _inputs(n, seed)
         want = _reference(stream, n, gam, nH, xn, alpha, Cc)
         got = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
@@ -55,6 +56,14 @@ def test_static_substep_matches_allocating_entry_point():
         torch.cuda.synchronize()
         assert float(got) == pytest.approx(float(want), rel=1e-5)
         assert float(got) > 0
+        if n == 777:
+            # and against the FP64 oracle of Eq. e:dtss, at the tolerance of the other
+            # substep tests
+            from oracle import oracle as O
+            ref = O.dt_substep(xn.cpu().double().numpy(), gam.cpu().double().numpy(),
+                               nH.cpu().double().numpy(), alpha, Cc)
+            assert float(got) == pytest.approx(ref, rel=1e-5)
+        del gam, nH, xn
 
 
 def test_static_substep_rejects_oversize_input():
