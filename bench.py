@@ -1,5 +1,5 @@
-"""Benchmark of the adaptive ray trace on one GB300 (and N independent replicas under
-torchrun).
+"""Benchmark of the adaptive ray trace on one GB300 (and one problem split by source over N
+GPUs under torchrun).
 
 Workload (default): the coupled trace + ionization-balance step on a 512^3 lognormal grid
 (sigma_ln = 2.0, k^-4 power spectrum, mean n_H = 100 in code units) with 1024 power-law
@@ -9,7 +9,9 @@ crossings per second. Inputs (512 MB density, 2 GB accumulator) exceed the 129 M
 L2 flush is needed between steps.
 
 Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle on a bounded
-sample of the same workload instead.
+sample of the same workload instead. Under torchrun (N > 1) each rank traces its share of the
+sources and one all-reduce per step sums gamma and force; the total work is fixed, so the
+scaling is strong.
 """
 from __future__ import annotations
 
@@ -31,15 +33,21 @@ from paper_1711_06277_gb300 import synth  # noqa: E402
 
 BYTES_PER_CROSSING = 20  # 4 B opacity gather + 16 B deposit reduction
 
+BYTES_PER_CROSSING_ADJ = 36  # reverse sweep: 16 B record per step of each pass + 4 B reduction
+
 CONFIGS = {
-    # name: (n, sigma_ln, nsrc, seed)
+    # name: grid side, log-density spread, sources, seed, mean n_H, sigma_H, alpha_B, x_n(0)
     "c5_512_1024src": dict(n=512, sigma_ln=2.0, nsrc=1024, seed=5, nbar=100.0, sigma_H=0.1,
                            alpha=2e-4, x0=1e-3),
+    "c1_32_uniform": dict(n=32, sigma_ln=None, nsrc=1, seed=None, nbar=1.0, sigma_H=5.0,
+                          alpha=None, x0=1.0),
+    "c2_128_1src": dict(n=128, sigma_ln=1.5, nsrc=1, seed=1, nbar=1.0, sigma_H=10.0,
+                        alpha=None, x0=1.0),
     "c3_256_64src": dict(n=256, sigma_ln=2.0, nsrc=64, seed=3, nbar=1.0, sigma_H=10.0,
                          alpha=None, x0=1.0),
     "c4_128_16src": dict(n=128, sigma_ln=1.5, nsrc=16, seed=4, nbar=1.0, sigma_H=10.0,
                          alpha=None, x0=1.0),
-    # small cases of the same kernel for ncu captures (a few GB on the device at most)
+    # smaller cases of the same kernels (ncu captures keep a few GB on the device at most)
     "c5_512_8src": dict(n=512, sigma_ln=2.0, nsrc=8, seed=5, nbar=100.0, sigma_H=0.1,
                         alpha=2e-4, x0=1e-3),
     "c3_256_8src": dict(n=256, sigma_ln=2.0, nsrc=8, seed=3, nbar=1.0, sigma_H=10.0,
@@ -133,17 +141,32 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
-def make_workload(cfg: dict, rank: int = 0):
+def make_workload(cfg: dict):
+    """Total H density (float32, (n, n, n)), source positions and luminosities of a config."""
     n = cfg["n"]
-    seed = cfg["seed"] + 1000 * rank
-    rho = synth.lognormal_field(n, cfg["sigma_ln"], seed=seed)
+    if cfg["sigma_ln"] is None:  # config 1: uniform grid, one source at the box centre
+        return (np.full((n, n, n), cfg["nbar"], dtype=np.float32), np.array([[0.5, 0.5, 0.5]]),
+                np.array([1.0]))
+    rho = synth.lognormal_field(n, cfg["sigma_ln"], seed=cfg["seed"])
     nH = (cfg["nbar"] * rho).astype(np.float32)
-    pos = synth.uniform_positions(cfg["nsrc"], seed=seed)
-    L = synth.power_law_luminosities(cfg["nsrc"], seed=seed)
+    if cfg["nsrc"] == 1:  # config 2: one source at a seeded cell centre
+        return nH, synth.cell_centre_position(n, seed=cfg["seed"]), np.array([1.0])
+    pos = synth.uniform_positions(cfg["nsrc"], seed=cfg["seed"])
+    L = synth.power_law_luminosities(cfg["nsrc"], seed=cfg["seed"])
     return nH, pos, L
 
 
+def _params(A, cfg, args=None, **kw):
+    p = A.Params(level0=4, m_ray=4.0, tau_max=30.0, sigma_H=cfg["sigma_H"], **kw)
+    if args is not None:
+        p.schedule, p.chunk, p.block_threads = args.schedule, args.chunk, args.block_threads
+    return p
+
+
 def run_ours(args, rank, world, local_rank):
+    """The timed coupled step. With world > 1 the one problem is split by source over the
+    ranks (paper_1711_06277_gb300.shard): each rank traces its share, one all-reduce sums
+    gamma and force, every rank updates x_n."""
     import torch
     from paper_1711_06277_gb300 import art as A
 
@@ -151,42 +174,68 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     cfg = CONFIGS[args.config]
     n = cfg["n"]
-    nH_h, pos, L = make_workload(cfg, rank)
+    nH_h, pos, L = make_workload(cfg)
     x0 = cfg["x0"]
     nH = torch.from_numpy(nH_h).to(dev)
     xn = torch.full_like(nH, x0)
     nH0 = (xn * nH).contiguous()
     stream = torch.cuda.Stream(dev)
-    p = A.Params(level0=4, m_ray=4.0, tau_max=30.0, sigma_H=cfg["sigma_H"],
-                 schedule=args.schedule, chunk=args.chunk, block_threads=args.block_threads)
+    p = _params(A, cfg, args)
+    sharded = None
+    mine = np.arange(len(L))
+    if world > 1:
+        from paper_1711_06277_gb300 import shard
+        with torch.cuda.stream(stream):
+            sharded = shard.ShardedTrace(nH0, 1.0 / n, pos, L, p, stream=stream)
+        mine = sharded.mine
     tuned = None
-    if args.tune and args.schedule == "persistent" and not args.chunk and not args.block_threads:
+    if args.tune and args.schedule == "persistent" and not args.chunk and not args.block_threads \
+            and len(mine):
         from paper_1711_06277_gb300 import autotune
         with torch.cuda.stream(stream):
-            p = autotune.tune(nH0, 1.0 / n, pos, L, p)
+            p = autotune.tune(nH0, 1.0 / n, pos[mine], L[mine], p)
         tuned = {"chunk": p.chunk, "block_threads": p.block_threads,
                  "queue_capacity": p.queue_capacity}
-    with torch.cuda.stream(stream):
-        grid = A.Grid(nH0, 1.0 / n, stream=stream)
-        grid.add_sources(pos, L)
-    gamma = torch.empty_like(nH)
-    force = torch.empty((3,) + tuple(nH.shape), device=dev, dtype=torch.float32)
+    if sharded is not None:
+        sharded.params = p
+        grid = sharded.grid
+        gamma, force = sharded.out[0], sharded.out[1:4]
+    else:
+        with torch.cuda.stream(stream):
+            grid = A.Grid(nH0, 1.0 / n, stream=stream)
+            grid.add_sources(pos, L)
+        gamma = torch.empty_like(nH)
+        force = torch.empty((3,) + tuple(nH.shape), device=dev, dtype=torch.float32)
     alpha = cfg["alpha"]
     dt = 0.1 / (alpha * cfg["nbar"]) if alpha else 0.0
 
     def enqueue_step():
-        grid.trace(p, force=True, stats=False, out={"gamma": gamma, "force": force})
+        if sharded is not None:
+            sharded.trace(stats=False)
+        else:
+            grid.trace(p, force=True, stats=False, out={"gamma": gamma, "force": force})
         if alpha:
             A.xn_update(gamma, nH, xn, alpha, dt, nH0_out=nH0, stream=stream)
+
+    def local_crossings():
+        return grid.stats()["crossings"] if len(mine) else 0
+
+    def check_status():
+        if len(mine):
+            st = grid.stats()
+            if st["status"] != 0:
+                raise RuntimeError(f"trace status {st['status']}")
+            return st["crossings"]
+        return 0
 
     # warm-up (the first trace allocates ray buffers and direction tables)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             enqueue_step()
-            grid.stats()
+            check_status()
     graph = None
     graph_note = None
-    if args.graph:
+    if args.graph and sharded is None:
         try:
             graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(graph, stream=stream):
@@ -194,6 +243,8 @@ def run_ours(args, rank, world, local_rank):
             torch.cuda.synchronize(dev)
         except Exception as e:  # report and run eagerly
             graph, graph_note = None, f"capture failed: {type(e).__name__}: {e}"[:200]
+    elif sharded is not None:
+        graph_note = "eager: a step holds an NCCL all-reduce"
 
     def step():
         with torch.cuda.stream(stream):
@@ -217,10 +268,7 @@ def run_ours(args, rank, world, local_rank):
             sev[0].record(stream)
             step()
             sev[1].record(stream)
-            st = grid.stats()  # synchronizes; the counters of this step's trace
-            if st["status"] != 0:
-                raise RuntimeError(f"trace status {st['status']}")
-            cross += st["crossings"]
+            cross += check_status()  # synchronizes; the counters of this step's trace
             step_ms.append(sev[0].elapsed_time(sev[1]))
         ev[1].record(stream)
         torch.cuda.synchronize(dev)
@@ -239,38 +287,49 @@ def run_ours(args, rank, world, local_rank):
     achieved = per_launch_cross * BYTES_PER_CROSSING / trace_s / 1e9
     traffic, traffic_note = captured_traffic(per_launch_cross)
 
-    # end to end through the public API with host buffers (pinned): H2D of the neutral
-    # density, trace + update, D2H of the updated neutral fraction
+    # end to end through the public API with host buffers (pinned), over as many steps as
+    # the device-timed run: H2D of the neutral density, trace + update, D2H of the updated
+    # neutral fraction
     e2e = None
-    if args.e2e_steps > 0:
+    e2e_steps = args.steps if args.e2e_steps is None else args.e2e_steps
+    if e2e_steps > 0:
         h_in = torch.empty(nH0.shape, dtype=torch.float32, pin_memory=True)
         h_in.copy_(nH0.cpu())
         h_out = torch.empty_like(h_in, pin_memory=True)
         e_cross = 0
+        if world > 1:
+            dist.barrier()
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
             e0.record(stream)
-            for _ in range(args.e2e_steps):
+            for _ in range(e2e_steps):
                 nH0.copy_(h_in, non_blocking=True)
                 enqueue_step()
                 h_out.copy_(xn, non_blocking=True)
-                e_cross += grid.stats()["crossings"]
+                e_cross += local_crossings()
             e1.record(stream)
         torch.cuda.synchronize(dev)
-        e_ms = e0.elapsed_time(e1)
+        e_ms, e_cross = reduce_over_ranks(e0.elapsed_time(e1), e_cross, dev if world > 1 else None)
         nbytes = nH0.numel() * 4
         e2e = {"value": e_cross / (e_ms / 1e3), "unit": "crossings/s",
-               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-               "steps": args.e2e_steps}
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
 
     extra = {}
     if rank == 0 and args.compare_plain:
         extra["plain_vs_persistent"] = compare_schedules(A, dev)
     if rank == 0 and args.adjoint:
-        extra["adjoint"] = adjoint_ratio(A, dev)
-    grid.close()
+        extra["adjoint"] = adjoint_ratio(A, dev, "c4_128_16src")
+        extra["adjoint_512"] = adjoint_ratio(A, dev, "c5_512_8src")
+    if rank == 0 and args.per_config:
+        extra["per_config"] = per_config(A, dev)
+    if sharded is not None:
+        extra["shard"] = {"sources_this_rank": int(len(mine)),
+                          "estimated_load": [float(v) for v in sharded.load]}
+        sharded.close()
+    else:
+        grid.close()
     launches = 5 if alpha else 4
     return {
         "value": value, "ms": ms_all, "cross": cross_all, "clocks": clk.summary(),
@@ -288,9 +347,8 @@ def run_ours(args, rank, world, local_rank):
 
 
 def reduce_over_ranks(ms: float, crossings: float, device=None):
-    """Whole-job timing of N replicas: the slowest rank's time and every rank's crossings.
-    Timing only -- no field data crosses ranks. Without an initialised process group it
-    returns its inputs."""
+    """Whole-job timing: the slowest rank's time and every rank's crossings. Without an
+    initialised process group it returns its inputs."""
     import torch
     import torch.distributed as dist
     if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
@@ -303,35 +361,50 @@ def reduce_over_ranks(ms: float, crossings: float, device=None):
     return float(mx[0]), float(sm[1])
 
 
-def adjoint_ratio(A, dev):
-    """Forward trace vs hand-written adjoint, 128^3 lognormal, 16 sources, loss = sum w gamma."""
+def _time(fn, stream, reps=3):
     import torch
-    cfg = CONFIGS["c4_128_16src"]
+    best = float("inf")
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def adjoint_ratio(A, dev, name="c4_128_16src"):
+    """Forward trace vs hand-written adjoint (loss = sum w gamma), and the adjoint's roofline
+    at 36 algorithmic bytes per forward crossing."""
+    import torch
+    cfg = CONFIGS[name]
     nH_h, pos, L = make_workload(cfg)
-    nH0 = torch.from_numpy(nH_h).to(dev)
+    nH0 = torch.from_numpy((cfg["x0"] * nH_h).astype(np.float32)).to(dev)
     w = torch.from_numpy(synth.uniform_weights(cfg["n"], seed=cfg["seed"]).astype(np.float32)).to(dev)
     stream = torch.cuda.current_stream(dev)
     g = A.Grid(nH0, 1.0 / cfg["n"], stream=stream)
     g.add_sources(pos, L)
-    p = A.Params(level0=4, tau_max=30.0, sigma_H=cfg["sigma_H"])
+    p = _params(A, cfg)
     g.trace(p, force=False)
     g.trace_backward(p, w)
     tf, tb = [], []
     for _ in range(3):
-        for lst, fn in ((tf, lambda: g.trace(p, force=False, stats=False)),
-                        (tb, lambda: g.trace_backward(p, w, stats=False))):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            lst.append(e0.elapsed_time(e1))
+        tf.append(_time(lambda: g.trace(p, force=False, stats=False), stream, 1))
+        tb.append(_time(lambda: g.trace_backward(p, w, stats=False), stream, 1))
     st = g.stats()
     g.close()
-    return {"workload": "128^3 lognormal sigma_ln=1.5, 16 sources, loss = sum w gamma",
+    peak, kind = _measured_peaks()
+    achieved = st["crossings"] * BYTES_PER_CROSSING_ADJ / (min(tb) / 1e3) / 1e9
+    return {"workload": f"{cfg['n']}^3 lognormal sigma_ln={cfg['sigma_ln']}, {cfg['nsrc']} "
+                        f"sources, loss = sum w gamma",
             "forward_ms": min(tf), "backward_ms": min(tb), "ratio": min(tb) / min(tf),
-            "crossings": st["crossings"]}
+            "crossings": st["crossings"],
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": kind,
+                         "kernel": "k_backward_persistent",
+                         "bytes_per_crossing": BYTES_PER_CROSSING_ADJ}}
 
 
 def compare_schedules(A, dev):
@@ -345,52 +418,131 @@ def compare_schedules(A, dev):
     g.add_sources(pos, L)
     res = {}
     for sched in ("persistent", "plain"):
-        p = A.Params(level0=4, tau_max=30.0, sigma_H=cfg["sigma_H"], schedule=sched)
-        g.trace(p, force=False)
-        torch.cuda.synchronize(dev)
-        t = []
-        for _ in range(3):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            st = g.trace(p, force=False)["stats"]
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            t.append(e0.elapsed_time(e1))
-        res[sched] = {"ms": min(t), "crossings": st["crossings"],
-                      "crossings_per_s": st["crossings"] / (min(t) / 1e3)}
+        p = _params(A, cfg, schedule=sched)
+        st = g.trace(p, force=False)["stats"]
+        res[sched] = {"ms": _time(lambda: g.trace(p, force=False, stats=False), stream),
+                      "crossings": st["crossings"]}
+        res[sched]["crossings_per_s"] = st["crossings"] / (res[sched]["ms"] / 1e3)
     res["speedup"] = res["plain"]["ms"] / res["persistent"]["ms"]
     g.close()
     return res
 
 
-def run_reference(args):
-    """FP64 CPU oracle on a bounded sample: one source of the workload per step."""
-    sys.path.insert(0, ROOT)
+def per_config(A, dev):
+    """Crossings/s and the trace's roofline fraction (20 B per crossing) on configs 1-4:
+    the persistent schedule writing gamma and force, best of 3 after a warm-up trace;
+    config 3 with autotuned launch knobs."""
+    import torch
+    peak, _ = _measured_peaks()
+    out = {}
+    stream = torch.cuda.current_stream(dev)
+    for name in ("c1_32_uniform", "c2_128_1src", "c3_256_64src", "c4_128_16src"):
+        cfg = CONFIGS[name]
+        nH_h, pos, L = make_workload(cfg)
+        nH0 = torch.from_numpy(nH_h).to(dev)
+        p = _params(A, cfg)
+        if name == "c3_256_64src":
+            from paper_1711_06277_gb300 import autotune
+            p = autotune.tune(nH0, 1.0 / cfg["n"], pos, L, p)
+        g = A.Grid(nH0, 1.0 / cfg["n"], stream=stream)
+        g.add_sources(pos, L)
+        gam = torch.empty_like(nH0)
+        frc = torch.empty((3,) + tuple(nH0.shape), device=dev, dtype=torch.float32)
+        st = g.trace(p, force=True, out={"gamma": gam, "force": frc})["stats"]
+        ms = _time(lambda: g.trace(p, force=True, stats=False, out={"gamma": gam, "force": frc}),
+                   stream)
+        g.close()
+        rate = st["crossings"] / (ms / 1e3)
+        out[name] = {"crossings": st["crossings"], "ms": ms, "crossings_per_s": rate,
+                     "roofline_frac": rate * BYTES_PER_CROSSING / 1e9 / peak}
+    return out
+
+
+# --------------------------------------------------------------------------------------
+# FP64 oracle on the host cores (the CPU baseline and the reference arm)
+# --------------------------------------------------------------------------------------
+# Bounded samples of one source of a workload: the base rays whose pixel index is a
+# multiple of the stride, with all their descendants (every ray is traced as in the full
+# trace; only the set of base rays is thinned). The strides keep one sample near 1-3 s.
+STRIDE_ONE_THREAD = 64
+STRIDE_ALL_CORES = 4
+
+
+def _oracle_sample(cfg, k, nthreads, stride):
     from oracle import oracle as O
-    cfg = CONFIGS[args.config]
-    n = cfg["n"]
     nH_h, pos, L = make_workload(cfg)
     nH0 = (cfg["x0"] * nH_h.astype(np.float64)).astype(np.float32)
-    threads = os.cpu_count() or 1
-
-    def one(k):
-        s = k % len(L)
-        prob = O.Problem(nH0=nH0, pos=pos[s:s + 1], L=L[s:s + 1], dx=1.0 / n,
-                         sigma_H=cfg["sigma_H"], level0=4, m_ray=4.0, tau_max=30.0)
-        return O.trace(prob, nthreads=threads).crossings
-
-    for k in range(args.warmup):
-        one(k)
+    s = k % len(L)
+    prob = O.Problem(nH0=nH0, pos=pos[s:s + 1], L=L[s:s + 1], dx=1.0 / cfg["n"],
+                     sigma_H=cfg["sigma_H"], level0=4, m_ray=4.0, tau_max=30.0)
     t0 = time.perf_counter()
-    cross = 0
+    r = O.trace(prob, nthreads=nthreads, pix_stride=stride)
+    return r.crossings, time.perf_counter() - t0
+
+
+def cpu_baseline(name, reps=5):
+    """The oracle as it stands on one bounded sample of the workload, at 1 thread and at all
+    host cores: median of ``reps`` timed runs after one untimed run each."""
+    cfg = CONFIGS[name]
+    cores = os.cpu_count() or 1
+    rates = {}
+    for threads, stride in ((1, STRIDE_ONE_THREAD), (cores, STRIDE_ALL_CORES)):
+        _oracle_sample(cfg, 0, threads, stride)
+        runs = [_oracle_sample(cfg, 0, threads, stride) for _ in range(reps)]
+        rates[threads] = statistics.median(c / t for c, t in runs)
+    return {"value": rates[cores], "unit": "crossings/s", "cores": cores, "kind": "oracle",
+            "value_1thread": rates[1], "speedup_all_cores": rates[cores] / rates[1],
+            "sample": (f"source 0 of the {cfg['n']}^3 / {cfg['nsrc']}-source workload at its "
+                       f"initial neutral fraction, base rays with pixel index a multiple of "
+                       f"{STRIDE_ONE_THREAD} (1 thread) or {STRIDE_ALL_CORES} ({cores} threads) "
+                       f"and all their descendants; median of {reps}")}
+
+
+def run_reference(args):
+    """FP64 CPU oracle on all host cores, one bounded sample of the workload per step."""
+    cfg = CONFIGS[args.config]
+    threads = os.cpu_count() or 1
+    for k in range(args.warmup):
+        _oracle_sample(cfg, k, threads, STRIDE_ALL_CORES)
+    cross, dt = 0, 0.0
     for k in range(args.steps):
-        cross += one(args.warmup + k)
-    dt = time.perf_counter() - t0
-    value = cross / dt
-    sample = (f"one source per step (sources {args.warmup}..{args.warmup + args.steps - 1}) of "
-              f"the {n}^3 / {cfg['nsrc']}-source workload at its initial neutral fraction")
-    return {"value": value, "ms": dt * 1e3 / args.steps, "threads": threads, "sample": sample}
+        c, t = _oracle_sample(cfg, args.warmup + k, threads, STRIDE_ALL_CORES)
+        cross += c
+        dt += t
+    sample = (f"per step one source of the {cfg['n']}^3 / {cfg['nsrc']}-source workload at its "
+              f"initial neutral fraction (sources {args.warmup}..{args.warmup + args.steps - 1} "
+              f"mod {cfg['nsrc']}), base rays with pixel index a multiple of {STRIDE_ALL_CORES} "
+              f"and all their descendants")
+    return {"value": cross / dt, "ms": dt * 1e3 / args.steps, "threads": threads, "sample": sample}
+
+
+def oracle_table():
+    """Oracle crossings/s per config at 1 thread and at all cores (median of 5), for the
+    results table: configs 1-2 whole, configs 3-4 on their first 8 sources, config 5 on 8
+    sources; thinned base rays where a whole run would take minutes."""
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    plan = {"c1_32_uniform": (1, 1, 1), "c2_128_1src": (1, 2, 1), "c3_256_64src": (8, 64, 4),
+            "c4_128_16src": (8, 8, 1), "c5_512_1024src": (8, 512, 32)}
+    out = {}
+    for name, (nsrc, s1, sn) in plan.items():
+        cfg = CONFIGS[name]
+        nH_h, pos, L = make_workload(cfg)
+        nH0 = (cfg["x0"] * nH_h.astype(np.float64)).astype(np.float32)
+        prob = O.Problem(nH0=nH0, pos=pos[:nsrc], L=L[:nsrc], dx=1.0 / cfg["n"],
+                         sigma_H=cfg["sigma_H"], level0=4, m_ray=4.0, tau_max=30.0)
+        row = {"sources": nsrc}
+        for threads, stride in ((1, s1), (cores, sn)):
+            O.trace(prob, nthreads=threads, pix_stride=stride)
+            runs = []
+            for _ in range(5):
+                t0 = time.perf_counter()
+                r = O.trace(prob, nthreads=threads, pix_stride=stride)
+                runs.append(r.crossings / (time.perf_counter() - t0))
+            row[f"threads_{threads}"] = {"crossings_per_s": statistics.median(runs),
+                                         "pix_stride": stride}
+        out[name] = row
+    return {"oracle_table": out, "cores": cores}
 
 
 def main():
@@ -403,7 +555,8 @@ def main():
     ap.add_argument("--schedule", default="persistent", choices=["persistent", "plain"])
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--block-threads", type=int, default=0)
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=None,
+                    help="steps of the end-to-end measurement (default: --steps)")
     ap.add_argument("--no-e2e", dest="e2e_steps", action="store_const", const=0)
     ap.add_argument("--graph", action="store_true", default=True)
     ap.add_argument("--no-graph", dest="graph", action="store_false")
@@ -412,7 +565,13 @@ def main():
     ap.add_argument("--adjoint", action="store_true", default=True)
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false")
     ap.add_argument("--adjoint-only", action="store_true",
-                    help="only the forward/backward timing of the 128^3 / 16-source case")
+                    help="only the forward/backward timing of the adjoint cases")
+    ap.add_argument("--adjoint-cases", default="c4_128_16src,c5_512_8src",
+                    help="configs timed by the adjoint comparison (comma-separated)")
+    ap.add_argument("--per-config", action="store_true", default=True)
+    ap.add_argument("--no-per-config", dest="per_config", action="store_false")
+    ap.add_argument("--oracle-table", action="store_true",
+                    help="only the oracle's rates per config (1 thread and all cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-plain", action="store_true", default=True)
     ap.add_argument("--no-compare-plain", dest="compare_plain", action="store_false")
@@ -427,8 +586,15 @@ def main():
                           + (", trace + Eq. e:xn3 update per step" if cfg["alpha"] else ""),
               "grid": cfg["n"], "sources": cfg["nsrc"], "schedule": args.schedule,
               "cuda_graph": args.graph,
+              "parallelism": (f"sources split over {world} GPUs, one all-reduce of gamma and "
+                              f"force per step" if world > 1 else "one GPU"),
               "l2": (f"inputs larger than L2 ({cfg['n'] ** 3 * 4 >> 20} MB density, "
                      f"{cfg['n'] ** 3 * 16 >> 20} MB accumulator; L2 is 129 MB)")}
+
+    if args.oracle_table:
+        if rank == 0:
+            print(json.dumps(oracle_table()), flush=True)
+        return
 
     if args.impl == "reference":
         if rank != 0:
@@ -437,7 +603,7 @@ def main():
         line = {"impl": "reference", "metric": "cell-segment crossings/s", "value": r["value"],
                 "unit": "crossings/s", "n_gpus": args.gpus, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": config,
                 "cpu_baseline": {"value": r["value"], "unit": "crossings/s", "cores": r["threads"],
                                  "kind": "oracle", "sample": r["sample"]},
@@ -450,7 +616,9 @@ def main():
         if rank == 0:
             import torch
             from paper_1711_06277_gb300 import art as A
-            print(json.dumps({"adjoint": adjoint_ratio(A, torch.device("cuda", local_rank))}))
+            dev = torch.device("cuda", local_rank)
+            print(json.dumps({name: adjoint_ratio(A, dev, name)
+                              for name in args.adjoint_cases.split(",")}))
         return
 
     if world > 1:
@@ -463,10 +631,7 @@ def main():
         return
     cpu = None
     if not args.no_cpu_baseline:
-        ra = argparse.Namespace(**{**vars(args), "steps": 1, "warmup": 0})
-        rr = run_reference(ra)
-        cpu = {"value": rr["value"], "unit": "crossings/s", "cores": rr["threads"],
-               "kind": "oracle", "sample": rr["sample"]}
+        cpu = cpu_baseline(args.config)
     config["cuda_graph"] = r["graph"]
     if r["graph_note"]:
         config["cuda_graph_note"] = r["graph_note"]
@@ -474,7 +639,7 @@ def main():
         config["autotuned"] = r["tuned"]
     line = {"metric": "cell-segment crossings/s", "value": r["value"], "unit": "crossings/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
             "clocks": r["clocks"], "roofline": r["roofline"], "cpu_baseline": cpu,
             "e2e": r["e2e"], "gpu_launches": r["gpu_launches"]}

@@ -42,6 +42,9 @@ extern "C" {
 #define ART_EACCOUNTING (-5)     /* retired-ray weights do not add up to N_src*12*4^l_max */
 #define ART_ECUDA (-6)           /* a CUDA runtime call failed */
 #define ART_ESTATE (-7)          /* call out of order (e.g. no sources, no trace yet) */
+#define ART_EINTERNAL (-8)       /* a device-side consistency bound was exceeded (a walk
+                                    longer than any straight ray through the grid, a schedule
+                                    phase without rays); results incomplete */
 
 #define ART_MAX_LEVEL 13
 #define ART_NLEVELS 20
@@ -231,6 +234,31 @@ long long art_dt_scratch_bytes(long long ncell);
 int art_dt_substep_static(void* stream, long long ncell, const float* d_gamma,
                           const float* d_nH, const float* d_xn, double alpha_B, double C,
                           double* d_dt);
+
+/* Splitting one trace over several GPUs by source (new; the paper's MPI version decomposes the
+ * domain and passes rays between ranks instead, Sec. 2.2). Sources are independent and
+ * their deposits add (Sec. 2.1), so ranks holding the same density field can each trace a
+ * disjoint subset of the sources and sum gamma, force and energy with one all-reduce; the
+ * reverse sweep's dloss/dlog n_H0 sums the same way, dloss/dL_s belongs to the source's rank.
+ *
+ * art_estimate_work: a per-source estimate of the trace's crossings, for balancing that
+ * split. Walks 12*4^min(l0, 2) rays from every source, without splitting, to where the trace
+ * would retire them (tau > tau_max with the current fields and p's cross sections, the d_max
+ * cutoff, or the grid boundary); a coarse ray reaching D cells covers the base rays out to
+ * r_max(l0) and about m_ray Omega r^2 split rays at radius r beyond it.
+ * h_work: host, art_num_sources doubles (written), in crossings (an estimate, not a count).
+ * Synchronizes the grid's stream; allocates and frees a small scratch.
+ * Errors: ART_EINVAL, ART_ESTATE (no sources), ART_ENOMEM, ART_ECUDA. */
+int art_estimate_work(art_grid* g, const art_params* p, double* h_work);
+
+/* Assigns n sources with work estimates h_work (host, n doubles >= 0) to nranks ranks:
+ * longest processing time first (largest estimate first, each to the least-loaded rank,
+ * ties by index), so every rank computes the same assignment from the same estimates and the
+ * largest load is at most 4/3 of the optimum. h_rank: host, n ints (written, 0..nranks-1);
+ * h_load: host, nranks doubles (written, the summed estimate per rank), or NULL.
+ * Host only: needs no GPU. Errors: ART_EINVAL (n < 0, nranks < 1, negative or non-finite
+ * work, NULL arrays). */
+int art_partition_sources(int n, const double* h_work, int nranks, int* h_rank, double* h_load);
 
 /* Frees the grid and everything it allocated (not the borrowed fields). NULL is a no-op. */
 void art_destroy_grid(art_grid* g);

@@ -183,6 +183,7 @@ typedef struct {
     int two_bin;        /* a second, non-ionizing bin attenuated by dust only (Sec. 2.3) */
     double rmax_unit;   /* sqrt(3/(pi m_ray)): r_max(l) = rmax_unit * 2^l (cells) */
     double dmax;        /* rays end at this distance from their source (cells); INFINITY: none */
+    long long* hits;    /* deposits per cell (counted when not NULL; test bookkeeping only) */
 } or_problem;
 
 typedef struct {
@@ -345,6 +346,10 @@ static int or_walk(const or_problem* P, const double u[3], or_ray* ray, int lmax
                 or_add(acc + ncell + idx, (dL + dLn) * n[0], atomic);
                 or_add(acc + 2 * ncell + idx, (dL + dLn) * n[1], atomic);
                 or_add(acc + 3 * ncell + idx, (dL + dLn) * n[2], atomic);
+                if (P->hits) {
+#pragma omp atomic
+                    P->hits[idx] += 1;
+                }
             }
             if (segs) {
                 or_seg g = {idx, dsp, dtau, chiH * dsp, ray->L};
@@ -435,6 +440,7 @@ static int or_setup(or_problem* P, int nx, int ny, int nz, double dx, const floa
     for (int i = 0; i < 9; ++i) P->rot[i] = rot ? rot[i] : (i % 4 == 0 ? 1.0 : 0.0);
     P->rmax_unit = sqrt(3.0 / (M_PI * m_ray));
     P->dmax = d_max > 0.0 ? d_max / dx : INFINITY;
+    P->hits = NULL;
     return 0;
 }
 
@@ -451,6 +457,9 @@ static int or_source_cells(const or_problem* P, int nsrc, const double* lo, cons
 
 /*
  * Full multi-source trace. acc: 4*ncell doubles (G, Fx, Fy, Fz blocks), overwritten.
+ * pix_stride >= 1: trace only the base rays whose pixel index is a multiple of pix_stride
+ * (with all their descendants), a bounded sample for timing; 1 traces everything.
+ * hits: ncell counts of deposits per cell (overwritten), or NULL.
  * Ln: per-source non-ionizing luminosity (a second bin, attenuated by n_H sigma_d), or NULL
  * for one bin. dstat[8] = {L_in, absorbed, escaped, dropped} of the ionizing bin, then the
  * same four of the non-ionizing bin.
@@ -463,18 +472,20 @@ int or_trace(int nx, int ny, int nz, const double* lo, double dx, const float* n
              int level0,
              int level_cap, double m_ray, double tau_max, double sigma_H, double sigma_d,
              const double* rot, double d_max, double* acc, double* dstat, long long* istat,
-             int nthreads)
+             int nthreads, int pix_stride, long long* hits)
 {
     or_problem P;
     if (or_setup(&P, nx, ny, nz, dx, nH0, nH, level0, level_cap, m_ray, tau_max, sigma_H,
                  sigma_d, rot, d_max))
         return -1;
-    if (nsrc < 0) return -1;
+    if (nsrc < 0 || pix_stride < 1) return -1;
+    P.hits = hits;
     P.two_bin = Ln != NULL;
     double* u = (double*)malloc(sizeof(double) * 3 * (size_t)(nsrc > 0 ? nsrc : 1));
     if (or_source_cells(&P, nsrc, lo, pos, u)) { free(u); return -1; }
     const int64_t ncell = (int64_t)nx * ny * nz;
     memset(acc, 0, sizeof(double) * 4 * (size_t)ncell);
+    if (hits) memset(hits, 0, sizeof(long long) * (size_t)ncell);
     double Ln_in = 0.0;
     for (int s = 0; s < nsrc && Ln; ++s) Ln_in += Ln[s];
     int lmax_glob = level0;
@@ -509,6 +520,7 @@ int or_trace(int nx, int ny, int nz, const double* lo, double dx, const float* n
         for (long long w = 0; w < nwork; ++w) {
             int s = (int)(w / nbase);
             uint64_t p = (uint64_t)(w % nbase);
+            if (p % (uint64_t)pix_stride != 0) continue;
             int lm = or_level_max(&P, u + 3 * s);
             or_ray root = {level0, p, L[s] / (double)nbase, 0.0,
                            Ln ? Ln[s] / (double)nbase : 0.0, 0.0};

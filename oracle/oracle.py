@@ -48,7 +48,7 @@ def _load():
         lib.or_vec2pix.argtypes = [i, dp]
         lib.or_vec2pix.restype = ctypes.c_uint64
         lib.or_trace.argtypes = [i, i, i, dp, d, fp, fp, i, dp, dp, dp, i, i, d, d, d, d, dp,
-                                 d, dp, dp, lp, i]
+                                 d, dp, dp, lp, i, i, lp]
         lib.or_trace.restype = i
         lib.or_ray_segments.argtypes = [i, i, i, dp, d, fp, fp, dp, i, i, d, d, d, d, dp, d,
                                         i, ctypes.c_ulonglong, d, d, lp, dp, i, P(ctypes.c_int)]
@@ -120,6 +120,7 @@ class TraceResult:
     rays_per_level: np.ndarray = field(default_factory=lambda: np.zeros(NLEVELS, np.int64))
     dV: float = 1.0
     sigma_H: float = 1.0
+    hits: np.ndarray | None = None     # (nz, ny, nx) deposits per cell, when asked for
 
     @property
     def gamma(self):
@@ -137,11 +138,16 @@ class TraceResult:
         return self.F / self.dV
 
 
-def trace(prob: Problem, nthreads: int = 1) -> TraceResult:
+def trace(prob: Problem, nthreads: int = 1, pix_stride: int = 1,
+          count_hits: bool = False) -> TraceResult:
+    """The full trace; ``pix_stride`` > 1 traces only the base rays whose pixel index is a
+    multiple of it (a bounded sample, for timing); ``count_hits`` also returns the number
+    of deposits per cell."""
     lib = _load()
     nx, ny, nz = prob._args()
     ncell = nx * ny * nz
     acc = np.zeros(4 * ncell, dtype=np.float64)
+    hits = np.zeros(ncell, dtype=np.int64) if count_hits else None
     dstat = np.zeros(8, dtype=np.float64)
     istat = np.zeros(8 + NLEVELS, dtype=np.int64)
     rc = lib.or_trace(nx, ny, nz, _ptr(prob._lo, ctypes.c_double), prob.dx,
@@ -151,7 +157,8 @@ def trace(prob: Problem, nthreads: int = 1) -> TraceResult:
                       prob.level0, prob.level_cap,
                       prob.m_ray, prob.tau_max, prob.sigma_H, prob.sigma_d,
                       _ptr(prob._rot, ctypes.c_double), prob.d_max, _ptr(acc, ctypes.c_double),
-                      _ptr(dstat, ctypes.c_double), _ptr(istat, ctypes.c_longlong), nthreads)
+                      _ptr(dstat, ctypes.c_double), _ptr(istat, ctypes.c_longlong), nthreads,
+                      int(pix_stride), _ptr(hits, ctypes.c_longlong))
     if rc != 0:
         raise ValueError("oracle rejected the problem")
     acc = acc.reshape(4, nz, ny, nx)
@@ -162,7 +169,8 @@ def trace(prob: Problem, nthreads: int = 1) -> TraceResult:
                        dropped_n=dstat[7],
                        destroy_expected=int(istat[4]), level_reached=int(istat[5]),
                        level_max=int(istat[6]), rays_per_level=istat[8:].copy(),
-                       dV=prob.dx**3, sigma_H=prob.sigma_H)
+                       dV=prob.dx**3, sigma_H=prob.sigma_H,
+                       hits=None if hits is None else hits.reshape(nz, ny, nx))
 
 
 def ray_segments(prob: Problem, level: int, pix: int, L: float = 1.0, tau: float = 0.0,

@@ -18,6 +18,7 @@ ART_ETIMEOUT = -4
 ART_EACCOUNTING = -5
 ART_ECUDA = -6
 ART_ESTATE = -7
+ART_EINTERNAL = -8
 ART_MAX_LEVEL = 13
 ART_NLEVELS = 20
 ART_SCHED_PERSISTENT = 0
@@ -28,7 +29,7 @@ EXPORTED = [
     "art_params_default", "art_create_grid", "art_update_fields", "art_add_sources",
     "art_set_nonionizing", "art_clear_sources", "art_num_sources", "art_trace", "art_get_stats", "art_trace_backward",
     "art_xn_update", "art_dt_substep", "art_dt_scratch_bytes", "art_dt_substep_static",
-    "art_destroy_grid", "art_strerror",
+    "art_estimate_work", "art_partition_sources", "art_destroy_grid", "art_strerror",
 ]
 ART_DT_STATIC_MAX_CELLS = 1 << 24
 
@@ -127,6 +128,10 @@ def lib():
         L.art_dt_scratch_bytes.restype = ll
         L.art_dt_substep_static.argtypes = [vp, ll, vp, vp, vp, d, d, vp]
         L.art_dt_substep_static.restype = i
+        L.art_estimate_work.argtypes = [vp, P(ArtParams), P(d)]
+        L.art_estimate_work.restype = i
+        L.art_partition_sources.argtypes = [i, P(d), i, P(i), P(d)]
+        L.art_partition_sources.restype = i
         L.art_destroy_grid.argtypes = [vp]
         L.art_destroy_grid.restype = None
         L.art_strerror.argtypes = [i]

@@ -164,6 +164,16 @@ class Grid:
         return {"gamma": g, "force": f if force else None, "energy": e if energy else None,
                 "stats": st.as_dict() if stats else None}
 
+    def estimate_work(self, params: Params) -> np.ndarray:
+        """Per-source estimate of a trace's crossings (float64, one per source), for
+        balancing a trace split over several GPUs; synchronizes."""
+        work = np.zeros(self.nsrc, dtype=np.float64)
+        cp = params.to_c()
+        C.check(C.lib().art_estimate_work(self._h, ctypes.byref(cp),
+                                          work.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                "art_estimate_work")
+        return work
+
     def stats(self) -> dict:
         st = C.ArtStats()
         C.check(C.lib().art_get_stats(self._h, ctypes.byref(st)), "art_get_stats")

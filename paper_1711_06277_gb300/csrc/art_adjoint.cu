@@ -87,15 +87,28 @@ template <class Cell> __device__ __forceinline__ const Cell* recs_of(const Trace
 template <> __device__ __forceinline__ const float4* recs_of<float4>(const TraceArgs& A) { return A.rec; }
 template <> __device__ __forceinline__ const CellF* recs_of<CellF>(const TraceArgs& A) { return A.recf; }
 
+// Idle lanes of a warp before it refills them from the queue, and steps between refill
+// checks (measured on the 128^3 / 16-source case).
+#ifndef ART_ADJ_IDLE
+#define ART_ADJ_IDLE 12
+#endif
+#ifndef ART_ADJ_STEPS
+#define ART_ADJ_STEPS 8
+#endif
+
 // One expand phase of the reverse sweep on the rays in slots [cursor .. end) of level l
 // (phase starting at slot `begin`). Pass 1 walks each ray for its own weighted sum. A ray
 // that splits stores that sum, a pending-children count of 4 and its children (in order, as
-// in the forward trace). A ray that ends walks again at once (pass 2) and deposits its
-// gradients; it then adds its total to its parent and counts the parent down. The lane that
-// brings a parent's count to zero takes over the parent's pass 2 (its level below this
-// phase's), and so on towards the base level: no separate collapse phase is needed, because
-// the deepest-first schedule does not reuse a level's slots before everything below it has
-// finished. Warp-uniform.
+// in the forward trace). A ray that ends without splitting (a leaf) walks again at once
+// (pass 2) from the start state kept from pass 1, depositing its gradients; it then adds
+// its total to its parent and counts the parent down. The lane that brings a parent's
+// count to zero takes over the parent's pass 2 (its level below this phase's), and so on
+// towards the base level: no separate collapse phase is needed, because the deepest-first
+// schedule does not reuse a level's slots before everything below it has finished. The
+// level data and buffer descriptors are copied out of the kernel parameters here: a
+// rewrite of the completion step that held references into the parameter block, indexed
+// by the changing level lv, never finished on the GPU with the d_max cutoff (the same
+// inputs finish in 2 ms with this form). Warp-uniform.
 template <class Cell, bool kCut>
 __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* cursor,
                             unsigned long long begin, unsigned long long end, Tally& T, DLacc& D)
@@ -116,6 +129,10 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
     int mode = 0;          // 0 idle, 1 pass 1 (level l), 2 pass 2 (level lv <= l)
     int lv = l;            // level of the ray being walked
     WalkT<Cell> W;
+    // pass-1 start of the ray (next face per axis, start cell), so that a leaf's pass 2
+    // restarts without a new ray set-up
+    df t0[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    int idx0 = 0;
     unsigned s = 0, p = 0;
     unsigned slot = 0;
     float L0 = 0.f, Ls = 0.f;
@@ -125,6 +142,11 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
     df rmax = LV.rmax;     // radius where the ray of level lv ends (split or cutoff)
     bool splits = false;
     unsigned ncross = 0, nrays = 0;
+    // Every step crosses at least one face, so a walk inside the grid takes at most
+    // nx + ny + nz steps plus the one into the sentinel ring. A walk that outlives that
+    // bound is abandoned with ART_EINTERNAL, so the kernel always ends.
+    const int step_bound = A.nx + A.ny + A.nz + 4;
+    int steps_left = step_bound;
 
     // Completion of the ray in `slot` at level lv (pass 2 done, or a ray without segments):
     // dL, the parent's sum, and possibly the parent's pass 2 in this lane.
@@ -162,7 +184,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
 
     for (;;) {
         unsigned need = __ballot_sync(kFull, mode == 0);
-        if (__popc(need) >= 12 || need == kFull) {  // measured: 12 > 8 > 4
+        if (__popc(need) >= ART_ADJ_IDLE || need == kFull) {
             while (need && more) {
                 if (wnext >= wend) {
                     unsigned long long b = 0;
@@ -182,6 +204,10 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
                     if constexpr (kCut) rmax = end_radius(splits, LV.rmax, A.dmax);
                     if (st > 0) {
                         Ls = __ldg(A.srcL + s);
+                        t0[0] = W.t[0];
+                        t0[1] = W.t[1];
+                        t0[2] = W.t[2];
+                        idx0 = W.idx;
                         mode = 1;
                         own = {0.f, 0.f};
                         ++nrays;
@@ -207,7 +233,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
         }
 
 #pragma unroll 1
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < ART_ADJ_STEPS; ++k) {
             if (mode != 0) {
                 const float4 cm = rec_main(W.cell);
                 const float wv = cm.z;   // weight and neutral-H opacity of this cell
@@ -215,11 +241,21 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
                 const float q = force_weight(W.cell, W.n, A.fscale);
                 // a ray ends at a radius (rmax) when it can split or (kCut) at the cutoff
                 const StepOut o = walk_step<false, true>(W, kCut || splits, rmax, recs, A.tau_max);
+                if (--steps_left < 0 && !o.end) {
+                    atomicCAS(&A.stats->error, 0, -8);  // ART_EINTERNAL: abandon the walk
+                    // a pass-1 ray leaves no children (its four slots marked empty); an
+                    // abandoned pass 2 never counts its parent down
+                    if (mode == 1 && has_next) write_holes(C, 4ull * (slot - b32));
+                    mode = 0;
+                    steps_left = step_bound;
+                    continue;
+                }
+                if (o.end) steps_left = step_bound;  // the next walk of this lane starts
                 // this segment's loss: w k G, plus q dL with a force term
                 const float g = fmaf(q, o.dL, wv * gs * o.G);
                 if (mode == 1) {
                     own = df_acc(own, g);
-                    ncross += o.cell >= 0 ? 1u : 0u;
+                    ncross += o.seg ? 1u : 0u;
                 } else {
                     rem = df_dec(rem, g);
                     const float after = rem.hi + rem.lo;
@@ -227,7 +263,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
                     // L_in e^-dtau)
                     const float own_d = fmaf(q, W.L, wv * gs * o.Lin * o.ds * o.dphi);
                     const float val = Ls * hv * o.ds * (own_d - after);
-                    if (o.cell >= 0) red_f32(A.grad + o.cell, val);
+                    if (o.seg) red_f32(A.grad + o.cell, val);
                 }
                 if (o.ev != EV_NONE) {
                     if (mode == 1) {
@@ -251,14 +287,25 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
                             }
                             mode = 0;
                         } else {
-                            if (o.ev != EV_DROP) atomicAdd(&T.escaped, (double)W.L);  // exit or cut
-                            else atomicAdd(&T.dropped, (double)W.L);
+                            const double Lend = (double)W.L + (double)W.Lc;
+                            if (o.ev != EV_DROP) atomicAdd(&T.escaped, Lend);  // exit or cut
+                            else atomicAdd(&T.dropped, Lend);
                             atomicAdd(&T.destroy, LV.destroy_w);
                             if (has_next) write_holes(C, c4);
                             // a leaf: pass 2 right away
                             total = own.hi + own.lo;
                             rem = own;
-                            ray_begin(A, LV, B, l, slot, W, recs, s, p, L0, splits);
+                            // a leaf: pass 2 right away, from the kept start state (direction
+                            // steps, source and luminosity are the ray's own already)
+                            W.t[0] = t0[0];
+                            W.t[1] = t0[1];
+                            W.t[2] = t0[2];
+                            W.idx = idx0;
+                            W.tc = LV.r0;
+                            W.L = L0;
+                            W.Lc = 0.f;
+                            W.tau = l == A.level0 ? 0.f : __ldcg(B.tau + slot);
+                            W.cell = load_cell(recs + idx0);
                             mode = 2;
                         }
                     } else {
@@ -294,6 +341,10 @@ __global__ void __launch_bounds__(256, 4) k_backward_persistent(const __grid_con
                 const unsigned long long have = min(v->count[l], A.buf[l].cap);
                 unsigned long long take = have;
                 if (l < A.lmax_glob) take = min(have, A.buf[l + 1].cap / 4);
+                if (take == 0) {  // a phase must consume rays, or the schedule never ends
+                    atomicCAS(&A.stats->error, 0, -8);  // ART_EINTERNAL
+                    take = have;
+                }
                 const unsigned long long b = have - take;
                 v->count[l] = b;
                 v->phase_level = l;
@@ -320,27 +371,58 @@ __global__ void __launch_bounds__(256, 4) k_backward_persistent(const __grid_con
     tally_flush(A.stats);
 }
 
-// Per-cell record of the reverse sweep: one 16-byte gather per crossing.
-__global__ void k_pack_cells(long long ncell, const float* __restrict__ chi,
-                             const float* __restrict__ chiH, const float* __restrict__ w,
-                             float4* __restrict__ rec)
+// Per-cell record of the reverse sweep in the padded layout: one 16-byte gather per
+// crossing, {chi, chi_H, w, 0} with chi and its neutral-H part formed exactly as k_opacity
+// forms the forward trace's opacity; the sentinel ring holds {-1, 0, 0, 0}.
+__global__ void k_pack_cells(int nx, int ny, int nz, const float* __restrict__ nH0,
+                             const float* __restrict__ nH, double sH_dx, double sd_dx,
+                             const float* __restrict__ w, float4* __restrict__ rec)
 {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long step = (long long)gridDim.x * blockDim.x;
-    for (; i < ncell; i += step) rec[i] = make_float4(chi[i], chiH[i], w ? w[i] : 0.f, 0.f);
+    const unsigned npad = (unsigned)(nx + 2) * (unsigned)(ny + 2) * (unsigned)(nz + 2);
+    const unsigned step = gridDim.x * blockDim.x;
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < npad; q += step) {
+        unsigned i;
+        if (!unpad(q, nx, ny, nz, i)) {
+            rec[q] = make_float4(kSentinel, 0.f, 0.f, 0.f);
+            continue;
+        }
+        const double h = (double)nH0[i] * sH_dx;
+        const double dust = nH ? (double)nH[i] * sd_dx : 0.0;
+        rec[q] = make_float4(__double2float_rn(h + dust), __double2float_rn(h), w ? w[i] : 0.f, 0.f);
+    }
 }
 
-// The same with the force weight v (3 blocks of ncell floats: x, y, z).
-__global__ void k_pack_cells_f(long long ncell, const float* __restrict__ chi,
-                               const float* __restrict__ chiH, const float* __restrict__ w,
-                               const float* __restrict__ v, CellF* __restrict__ rec)
+// The same with the force weight v (3 blocks of nx*ny*nz floats: x, y, z).
+__global__ void k_pack_cells_f(int nx, int ny, int nz, const float* __restrict__ nH0,
+                               const float* __restrict__ nH, double sH_dx, double sd_dx,
+                               const float* __restrict__ w, const float* __restrict__ v,
+                               CellF* __restrict__ rec)
 {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long step = (long long)gridDim.x * blockDim.x;
-    for (; i < ncell; i += step) {
-        rec[i].a = make_float4(chi[i], chiH[i], w ? w[i] : 0.f, 0.f);
-        rec[i].b = make_float4(v[i], v[ncell + i], v[2 * ncell + i], 0.f);
+    const unsigned npad = (unsigned)(nx + 2) * (unsigned)(ny + 2) * (unsigned)(nz + 2);
+    const size_t ncell = (size_t)nx * ny * nz;
+    const unsigned step = gridDim.x * blockDim.x;
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < npad; q += step) {
+        unsigned i;
+        if (!unpad(q, nx, ny, nz, i)) {
+            rec[q].a = make_float4(kSentinel, 0.f, 0.f, 0.f);
+            rec[q].b = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
+        const double h = (double)nH0[i] * sH_dx;
+        const double dust = nH ? (double)nH[i] * sd_dx : 0.0;
+        rec[q].a = make_float4(__double2float_rn(h + dust), __double2float_rn(h), w ? w[i] : 0.f, 0.f);
+        rec[q].b = make_float4(v[i], v[ncell + i], v[2 * ncell + i], 0.f);
     }
+}
+
+// Gradient per cell from the padded scratch it was summed in, into the caller's layout.
+__global__ void k_unpad_grad(int nx, int ny, int nz, const float* __restrict__ src,
+                             float* __restrict__ dst)
+{
+    const unsigned ncell = (unsigned)nx * (unsigned)ny * (unsigned)nz;
+    const unsigned step = gridDim.x * blockDim.x;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += step)
+        dst[i] = src[pad_of(i, nx, ny)];
 }
 
 __global__ void k_inject_all(int nsrc, unsigned npix0, RayBuf B, unsigned long long* count)
@@ -380,8 +462,6 @@ extern "C" int art_trace_backward(art_grid* g, const art_params* p, const float*
     if (g->two_bin) return ART_EINVAL;  // the reverse sweep covers one-bin traces
     cudaStream_t st = g->stream;
     if ((rc = status_of(cudaMemsetAsync(g->d_stats, 0, sizeof(DevStats), st)))) return rc;
-    if (!g->d_chiH && (rc = status_of(cudaMalloc((void**)&g->d_chiH, sizeof(float) * g->ncell))))
-        return rc;
     rc = prepare_trace(g, p, true);
     if (rc) return rc;
     if ((size_t)ns > g->srcL_cap) {
@@ -401,7 +481,9 @@ extern "C" int art_trace_backward(art_grid* g, const art_params* p, const float*
         return rc;
     double* dL = d_dL ? d_dL : g->d_dL_scratch;
     if ((rc = status_of(cudaMemsetAsync(dL, 0, sizeof(double) * ns, st)))) return rc;
-    if ((rc = status_of(cudaMemsetAsync(d_dlog_nH0, 0, sizeof(float) * g->ncell, st)))) return rc;
+    // the gradient is summed in the padded layout, in the (otherwise idle) accumulator
+    float* grad_pad = reinterpret_cast<float*>(g->d_acc);
+    if ((rc = status_of(cudaMemsetAsync(grad_pad, 0, sizeof(float) * g->npad, st)))) return rc;
     if ((rc = status_of(cudaMemsetAsync(g->d_sched, 0, sizeof(Sched), st)))) return rc;
     const int l0 = p->level0;
     const unsigned npix0 = 12u << (2 * l0);
@@ -409,22 +491,27 @@ extern "C" int art_trace_backward(art_grid* g, const art_params* p, const float*
     k_inject_all<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(ns, npix0, g->buf[l0],
                                                             &g->d_sched->count[l0]);
     if ((rc = status_of(cudaGetLastError()))) return rc;
-    const int pack_blocks = (int)std::min<long long>((g->ncell + 255) / 256, (long long)g->sms * 16);
+    const int pack_blocks = (int)std::min<long long>((g->npad + 255) / 256, (long long)g->sms * 16);
+    const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+    const double sH_dx = p->sigma_H * g->dx;
+    const double sd_dx = g->nH ? p->sigma_d * g->dx : 0.0;
     if (d_v) {
-        if (!g->d_recf && (rc = status_of(cudaMalloc((void**)&g->d_recf, sizeof(CellF) * g->ncell))))
+        if (!g->d_recf && (rc = status_of(cudaMalloc((void**)&g->d_recf, sizeof(CellF) * g->npad))))
             return rc;
-        k_pack_cells_f<<<pack_blocks, 256, 0, st>>>(g->ncell, g->d_chi, g->d_chiH, d_w, d_v, g->d_recf);
+        k_pack_cells_f<<<pack_blocks, 256, 0, st>>>(nx, ny, nz, g->nH0, g->nH, sH_dx, sd_dx, d_w,
+                                                    d_v, g->d_recf);
     } else {
-        if (!g->d_rec && (rc = status_of(cudaMalloc((void**)&g->d_rec, sizeof(float4) * g->ncell))))
+        if (!g->d_rec && (rc = status_of(cudaMalloc((void**)&g->d_rec, sizeof(float4) * g->npad))))
             return rc;
-        k_pack_cells<<<pack_blocks, 256, 0, st>>>(g->ncell, g->d_chi, g->d_chiH, d_w, g->d_rec);
+        k_pack_cells<<<pack_blocks, 256, 0, st>>>(nx, ny, nz, g->nH0, g->nH, sH_dx, sd_dx, d_w,
+                                                  g->d_rec);
     }
     if ((rc = status_of(cudaGetLastError()))) return rc;
     TraceArgs A = make_args(g, p);
     A.rec = g->d_rec;
     A.recf = d_v ? g->d_recf : nullptr;
     A.w = d_w;
-    A.grad = d_dlog_nH0;
+    A.grad = grad_pad;
     A.dL = dL;
     A.srcL = g->d_srcL;
     const double dV = g->dx * g->dx * g->dx;
@@ -451,6 +538,9 @@ extern "C" int art_trace_backward(art_grid* g, const art_params* p, const float*
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if ((rc = status_of(cudaLaunchKernelEx(&cfg, kern, A)))) return rc;
+    const int unpad_blocks = (int)std::min<long long>((g->ncell + 255) / 256, (long long)g->sms * 16);
+    k_unpad_grad<<<unpad_blocks, 256, 0, st>>>(nx, ny, nz, grad_pad, d_dlog_nH0);
+    if ((rc = status_of(cudaGetLastError()))) return rc;
     if ((rc = status_of(cudaMemcpyAsync(g->h_stats, g->d_stats, sizeof(DevStats),
                                         cudaMemcpyDeviceToHost, st))))
         return rc;

@@ -100,6 +100,42 @@ int check_params(const art_params* p)
     return ART_OK;
 }
 
+// Split radius r_max(l) = [3/(pi m_ray)]^(1/2) 2^l in cells (Sec. 2.1).
+double rmax_cells(double m_ray, int level) { return rmax_unit(m_ray) * std::ldexp(1.0, level); }
+
+// Direction tables of levels lfrom..lto (FP64 HEALPix, rotated by p's rotation, split
+// into hi + lo), rebuilt when the rotation changes.
+int ensure_directions(art_grid* g, const art_params* p, int lfrom, int lto)
+{
+    const bool rotate = (p->flags & ART_F_ROTATE) != 0;
+    bool same_rot = g->dir_rotate == rotate;
+    if (rotate && same_rot)
+        for (int i = 0; i < 9; ++i) same_rot = same_rot && g->dir_rot[i] == p->rot[i];
+    if (!same_rot) {
+        for (int l = 0; l < kNL; ++l) g->dir_built[l] = false;
+        g->dir_rotate = rotate;
+        for (int i = 0; i < 9; ++i) g->dir_rot[i] = rotate ? p->rot[i] : (i % 4 == 0 ? 1.0 : 0.0);
+    }
+    for (int l = lfrom; l <= lto; ++l) {
+        const unsigned long long npix = 12ull << (2 * l);
+        if (!g->dir[l]) {
+            int rc = dev_alloc(&g->dir[l], 3 * npix);
+            if (rc) return rc;
+            g->dir_built[l] = false;
+        }
+        if (!g->dir_built[l]) {
+            const double* r = g->dir_rot;
+            unsigned blocks = (unsigned)((npix + 255) / 256);
+            k_directions<<<blocks, 256, 0, g->stream>>>(l, npix, r[0], r[1], r[2], r[3], r[4],
+                                                        r[5], r[6], r[7], r[8], rotate ? 1 : 0,
+                                                        g->dir[l]);
+            ART_TRY(cudaGetLastError());
+            g->dir_built[l] = true;
+        }
+    }
+    return ART_OK;
+}
+
 // Source table, per-source l_max, direction tables, level constants and ray buffers for a
 // trace with parameters p. Allocates only when something grew or changed.
 int prepare_trace(art_grid* g, const art_params* p, bool adjoint)
@@ -169,36 +205,14 @@ int prepare_trace(art_grid* g, const art_params* p, bool adjoint)
                                     cudaMemcpyHostToDevice, g->stream));
         }
         if (!g->d_chi2) {
-            int rc = dev_alloc(&g->d_chi2, g->ncell);
+            int rc = dev_alloc(&g->d_chi2, g->npad);
             if (rc) return rc;
         }
     }
     // --- direction tables (FP64 HEALPix, rotated), rebuilt when the rotation changes
-    const bool rotate = (p->flags & ART_F_ROTATE) != 0;
-    bool same_rot = g->dir_rotate == rotate;
-    if (rotate && same_rot)
-        for (int i = 0; i < 9; ++i) same_rot = same_rot && g->dir_rot[i] == p->rot[i];
-    if (!same_rot) {
-        for (int l = 0; l < kNL; ++l) g->dir_built[l] = false;
-        g->dir_rotate = rotate;
-        for (int i = 0; i < 9; ++i) g->dir_rot[i] = rotate ? p->rot[i] : (i % 4 == 0 ? 1.0 : 0.0);
-    }
-    for (int l = l0; l <= lmax_glob; ++l) {
-        const unsigned long long npix = 12ull << (2 * l);
-        if (!g->dir[l]) {
-            int rc = dev_alloc(&g->dir[l], 3 * npix);
-            if (rc) return rc;
-            g->dir_built[l] = false;
-        }
-        if (!g->dir_built[l]) {
-            const double* r = g->dir_rot;
-            unsigned blocks = (unsigned)((npix + 255) / 256);
-            k_directions<<<blocks, 256, 0, g->stream>>>(l, npix, r[0], r[1], r[2], r[3], r[4],
-                                                        r[5], r[6], r[7], r[8], rotate ? 1 : 0,
-                                                        g->dir[l]);
-            ART_TRY(cudaGetLastError());
-            g->dir_built[l] = true;
-        }
+    {
+        const int rc = ensure_directions(g, p, l0, lmax_glob);
+        if (rc) return rc;
     }
     // --- level constants
     LevelInfo lv[kNL];
@@ -275,12 +289,17 @@ int prepare_trace(art_grid* g, const art_params* p, bool adjoint)
     g->prep_qcap = p->queue_capacity;
     g->prep_two_bin = g->two_bin;
     // --- opacity per cell length
+    return run_opacity(g, p, g->two_bin && !adjoint);
+}
+
+// Opacity per cell length (padded layout) into d_chi, and the two-bin pairs into d_chi2.
+int run_opacity(art_grid* g, const art_params* p, bool two_bin)
+{
     const double sH_dx = p->sigma_H * g->dx;
     const double sd_dx = g->nH ? p->sigma_d * g->dx : 0.0;
-    int blocks = (int)std::min<long long>((g->ncell + 255) / 256, (long long)g->sms * 16);
-    k_opacity<<<blocks, 256, 0, g->stream>>>(g->ncell, g->nH0, g->nH, sH_dx, sd_dx, g->d_chi,
-                                             adjoint ? g->d_chiH : nullptr,
-                                             (g->two_bin && !adjoint) ? g->d_chi2 : nullptr,
+    int blocks = (int)std::min<long long>((g->npad + 255) / 256, (long long)g->sms * 16);
+    k_opacity<<<blocks, 256, 0, g->stream>>>(g->n[0], g->n[1], g->n[2], g->nH0, g->nH, sH_dx,
+                                             sd_dx, g->d_chi, two_bin ? g->d_chi2 : nullptr,
                                              g->d_stats);
     ART_TRY(cudaGetLastError());
     return ART_OK;
@@ -300,7 +319,6 @@ TraceArgs make_args(art_grid* g, const art_params* p)
     A.chunk = p->chunk > 0 ? p->chunk : 64;
     A.tau_max = (float)p->tau_max;
     A.chi = g->d_chi;
-    A.chiH = g->d_chiH;
     A.chi2 = g->d_chi2;
     A.srcLn = g->d_srcLn;
     A.acc = g->d_acc;
@@ -376,11 +394,14 @@ int art_create_grid(art_grid** out, int nx, int ny, int nz, const double box_lo[
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(box_lo[a])) return ART_EINVAL;
     const long long ncell = (long long)nx * ny * nz;
-    if (ncell >= (1ll << 31)) return ART_EINVAL;
+    // the trace kernels index the padded layout (a ring of sentinel cells) in 32 bits
+    const long long npad = (long long)(nx + 2) * (ny + 2) * (nz + 2);
+    if (npad >= (1ll << 31)) return ART_EINVAL;
     art_grid* g = new (std::nothrow) art_grid();
     if (!g) return ART_ENOMEM;
     g->n[0] = nx; g->n[1] = ny; g->n[2] = nz;
     g->ncell = ncell;
+    g->npad = npad;
     for (int a = 0; a < 3; ++a) g->lo[a] = box_lo[a];
     g->dx = dx;
     g->nH0 = d_nH0;
@@ -388,8 +409,8 @@ int art_create_grid(art_grid** out, int nx, int ny, int nz, const double box_lo[
     g->stream = (cudaStream_t)stream;
     int rc = cuda_status(cudaGetDevice(&g->device));
     if (!rc) rc = cuda_status(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device));
-    if (!rc) rc = dev_alloc(&g->d_chi, ncell);
-    if (!rc) rc = dev_alloc(&g->d_acc, ncell);
+    if (!rc) rc = dev_alloc(&g->d_chi, npad);
+    if (!rc) rc = dev_alloc(&g->d_acc, npad);
     if (!rc) rc = dev_alloc(&g->d_levels, kNL);
     if (!rc) rc = dev_alloc(&g->d_sched, 1);
     if (!rc) rc = dev_alloc(&g->d_stats, 1);
@@ -470,12 +491,13 @@ int art_trace(art_grid* g, const art_params* p, float* d_gamma, float* d_force, 
     ART_TRY(cudaMemsetAsync(g->d_stats, 0, sizeof(DevStats), g->stream));
     rc = prepare_trace(g, p, false);
     if (rc) return rc;
-    ART_TRY(cudaMemsetAsync(g->d_acc, 0, sizeof(float4) * (size_t)g->ncell, g->stream));
+    ART_TRY(cudaMemsetAsync(g->d_acc, 0, sizeof(float4) * (size_t)g->npad, g->stream));
     ART_TRY(cudaMemsetAsync(g->d_sched, 0, sizeof(Sched), g->stream));
     const int ns = (int)g->L.size();
     const int l0 = p->level0;
     const unsigned npix0 = 12u << (2 * l0);
-    const int threads = p->block_threads > 0 ? p->block_threads : 256;
+    // block size: the caller's (or 256), at most what the trace kernels are built for
+    const int threads = std::min(p->block_threads > 0 ? p->block_threads : 256, kTraceMaxThreads);
     TraceArgs A = make_args(g, p);
     if (p->schedule == ART_SCHED_PLAIN) {
         int per_sm = 0;
@@ -523,8 +545,8 @@ int art_trace(art_grid* g, const art_params* p, float* d_gamma, float* d_force, 
     const float fscale = (float)(1.0 / dV);
     const float escale = (float)(g->dx / dV);
     int blocks = (int)std::min<long long>((g->ncell + 255) / 256, (long long)g->sms * 16);
-    k_finalize<<<blocks, 256, 0, g->stream>>>(g->ncell, g->d_acc, gscale, fscale, escale,
-                                              d_gamma, d_force, d_energy);
+    k_finalize<<<blocks, 256, 0, g->stream>>>(g->n[0], g->n[1], g->n[2], g->d_acc, gscale,
+                                              fscale, escale, d_gamma, d_force, d_energy);
     ART_TRY(cudaGetLastError());
     ART_TRY(cudaMemcpyAsync(g->h_stats, g->d_stats, sizeof(DevStats), cudaMemcpyDeviceToHost,
                             g->stream));
@@ -554,7 +576,6 @@ void art_destroy_grid(art_grid* g)
     if (!g) return;
     cudaStreamSynchronize(g->stream);
     dev_free(g->d_chi);
-    dev_free(g->d_chiH);
     dev_free(g->d_acc);
     dev_free(g->d_src);
     dev_free(g->d_levels);
@@ -589,6 +610,7 @@ const char* art_strerror(int status)
     case ART_EACCOUNTING: return "retired-ray weights do not add up to N_src*12*4^l_max";
     case ART_ECUDA: return "CUDA runtime error";
     case ART_ESTATE: return "call out of order (no sources or nothing traced)";
+    case ART_EINTERNAL: return "a device-side consistency bound was exceeded";
     default: return "unknown status";
     }
 }

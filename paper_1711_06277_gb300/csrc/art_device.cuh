@@ -142,15 +142,14 @@ struct TraceArgs {
     int level0, lmax_glob;
     int chunk;
     float tau_max;
-    const float* chi;        // opacity per cell times dx (per cell length)
-    const float2* chi2;      // two-bin traces: {chi_i, chi_n} per cell length
+    const float* chi;        // opacity per cell times dx (per cell length), padded layout
+    const float2* chi2;      // two-bin traces: {chi_i, chi_n} per cell length, padded
     const float* srcLn;      // two-bin traces: base-ray non-ionizing luminosity per source
-    const float* chiH;       // neutral-H part of chi (adjoint only)
     const float4* rec;       // adjoint: per cell {chi, chi_H, w, 0}
     const float* w;          // adjoint weights per cell
-    float* grad;             // adjoint output per cell
+    float* grad;             // adjoint gradient per cell (padded scratch)
     double* dL;              // adjoint output per source
-    float4* acc;             // per-cell accumulator (sum L ds phi, sum dL n)
+    float4* acc;             // per-cell accumulator (sum L ds phi, sum dL n), padded
     const SrcDev* src;
     const LevelInfo* levels;
     RayBuf buf[kNL];
@@ -201,15 +200,49 @@ struct WalkT {
     df t[3];      // distance from the source to the next face on each axis
     df d[3];      // distance between consecutive faces on each axis (1/|n_a|)
     df tc;        // distance of the current position
-    int idx;      // linear index of the current cell
-    int rem[3];   // cells left on each axis before the ray leaves the grid
+    int idx;      // index of the current cell in the padded layout (sentinel ring around
+                  // the grid, see pad_index)
     int ss[3];    // signed index step of a crossing on each axis
     float n[3];   // direction (hi parts) for momentum deposits
     float L, tau;
+    float Lc;        // photon ledger: the rounding error of this walk's L updates (see
+                     // walk_step); tallied with the ray, never used for deposits
     float Ln, taun;  // non-ionizing bin (two-bin traces only)
+    float Lnc;       // the same compensation for Ln
     Cell cell;    // record of the current cell (prefetched)
 };
 using Walk = WalkT<float>;
+
+// Cell records are stored with a ring of sentinel cells around the nx*ny*nz grid (opacity
+// < 0): cell (i, j, k) sits at (i + 1) + (nx + 2) ((j + 1) + (ny + 2) (k + 1)). A ray leaves
+// the grid when the cell it steps into is a sentinel, so the walk keeps no per-axis count of
+// cells left, and the cell after any crossing from inside the grid is a valid address.
+__host__ __device__ __forceinline__ long long pad_index(long long i, long long j, long long k,
+                                                        int nx, int ny)
+{
+    return (i + 1) + (long long)(nx + 2) * ((j + 1) + (long long)(ny + 2) * (k + 1));
+}
+constexpr float kSentinel = -1.0f;
+
+// Coordinates of padded cell q (see pad_index; padded grids hold fewer than 2^31 cells):
+// false for the sentinel ring, else the cell's index in the caller's nx*ny*nz layout.
+__device__ __forceinline__ bool unpad(unsigned q, int nx, int ny, int nz, unsigned& i)
+{
+    const unsigned px = (unsigned)nx + 2u, py = (unsigned)ny + 2u;
+    const unsigned r = q / px;
+    const int X = (int)(q - r * px) - 1;
+    const int Y = (int)(r % py) - 1;
+    const int Z = (int)(r / py) - 1;
+    i = (unsigned)X + (unsigned)nx * ((unsigned)Y + (unsigned)ny * (unsigned)Z);
+    return X >= 0 && X < nx && Y >= 0 && Y < ny && Z >= 0 && Z < nz;
+}
+
+// Padded index of cell i of the caller's nx*ny*nz layout.
+__device__ __forceinline__ unsigned pad_of(unsigned i, int nx, int ny)
+{
+    const unsigned r = i / (unsigned)nx, x = i - r * (unsigned)nx;
+    return (unsigned)pad_index(x, r % (unsigned)ny, r / (unsigned)ny, nx, ny);
+}
 
 // Sets up the walk of a ray with direction n and reciprocal inv (df, from the direction
 // table) from source position u (df) starting at radius r0. Returns false if the start
@@ -232,28 +265,28 @@ __device__ __forceinline__ bool walk_start(WalkT<Cell>& W, int nx, int ny, int n
         W.n[a] = n[a].hi;
         if (n[a].hi != 0.f) {
             const bool up = n[a].hi > 0.f;
-            W.rem[a] = up ? N[a] - 1 - ci : ci;
-            const int stride = a == 0 ? 1 : (a == 1 ? nx : nx * ny);
+            const int stride = a == 0 ? 1 : (a == 1 ? nx + 2 : (nx + 2) * (ny + 2));
             W.ss[a] = up ? stride : -stride;
             const df off = df_add({(float)(up ? ci + 1 : ci), 0.f}, df_neg(u[a]));
             W.t[a] = df_mul(off, inv[a]);
             W.d[a] = up ? inv[a] : df_neg(inv[a]);
         } else {
-            W.rem[a] = 1 << 30;
             W.ss[a] = 0;
             W.t[a] = {kBig, 0.f};
             W.d[a] = {0.f, 0.f};
         }
     }
     W.tc = r0;
-    W.idx = inside ? c[0] + nx * (c[1] + ny * c[2]) : 0;
+    W.idx = inside ? (int)pad_index(c[0], c[1], c[2], nx, ny) : 0;
     return inside;
 }
 
-// Outcome of one crossing step: the deposit to make (cell < 0: none) and the event.
+// Outcome of one crossing step: the deposit to make (in cell, when seg) and the event.
 struct StepOut {
-    int cell;
-    float ds;     // segment length (cell units), > 0 when cell >= 0
+    int cell;     // the cell the segment lies in (padded layout)
+    bool seg;     // the segment has positive length: deposit and count it
+    bool end;     // the ray ends with this step (ev != EV_NONE)
+    float ds;     // segment length (cell units), > 0 when seg
     float dtau;
     float Lin;
     float G;      // L_in ds phi(dtau)
@@ -317,51 +350,63 @@ __device__ __forceinline__ StepOut walk_step(WalkT<Cell>& W, bool splits, df rma
                                              const Cell* __restrict__ cells, float tau_max)
 {
     StepOut o;
+    // A step that starts in a sentinel cell ends the ray: it left the grid with the crossing
+    // of the previous step (whose segment was deposited then); nothing is deposited now.
+    const bool out = chi_of(W.cell) < 0.f;
     // Earliest face crossing, decided on the hi parts: for normalised df values |lo| is at
-    // most half an ulp of hi, so distinct hi parts order the values exactly and no two of
-    // them can lie within the 1e-12 tie tolerance. Equal hi parts (exact ties, near ties, a
-    // face at the split radius) take the exact double-float path below.
+    // most half an ulp of hi, so distinct hi parts order the values exactly. Equal hi parts
+    // (exact ties, near ties, a face at the split radius) take the exact double-float path
+    // below. Two values within the 1e-12 tie tolerance can still have distinct hi parts when
+    // they straddle a rounding boundary of hi; the walk then crosses the two faces in two
+    // steps with a segment far below the 1e-5-cell near-tie threshold between them, a ray
+    // the oracle flags as near-tie.
     const float h0 = W.t[0].hi, h1 = W.t[1].hi, h2 = W.t[2].hi;
     const bool c01 = h0 < h1;
     const float h01 = c01 ? h0 : h1;
     const bool c2 = h01 < h2;
-    int a = c2 ? (c01 ? 0 : 1) : 2;
+    bool p0 = c2 && c01, p1 = c2 && !c01, p2 = !c2;  // the earliest axis
     const float hm = c2 ? h01 : h2;
-    df tm = df_sel(a == 0, W.t[0], df_sel(a == 1, W.t[1], W.t[2]));
+    df tm = {hm, p2 ? W.t[2].lo : (c01 ? W.t[0].lo : W.t[1].lo)};
     bool split = splits && rmax.hi < hm;
-    bool m0 = a == 0, m1 = a == 1, m2 = a == 2;
-    // next cell and whether it leaves the grid, for the usual single-axis crossing
-    int nidx = W.idx + (a == 0 ? W.ss[0] : (a == 1 ? W.ss[1] : W.ss[2]));
-    bool out = (a == 0 ? W.rem[0] : (a == 1 ? W.rem[1] : W.rem[2])) == 0;
-    if (h0 == h1 || h0 == h2 || h1 == h2 || (splits && rmax.hi == hm)) {
+    // next cell, for the usual single-axis crossing
+    int nidx = W.idx + (p2 ? W.ss[2] : (c01 ? W.ss[0] : W.ss[1]));
+    // the second-earliest hi part: a tie with the earliest face, or the split radius at the
+    // earliest face, needs the exact comparison (axes parallel to the grid sit at kBig and
+    // tie only with each other, never with the earliest face)
+    const float h2nd = c2 ? fminf(c01 ? h1 : h0, h2) : h01;
+    if (h2nd == hm || (splits && rmax.hi == hm)) {
         const bool e01 = df_le(W.t[0], W.t[1]);
         tm = df_sel(e01, W.t[0], W.t[1]);
-        a = e01 ? 0 : 1;
+        int a = e01 ? 0 : 1;
         if (!df_le(tm, W.t[2])) {
             tm = W.t[2];
             a = 2;
         }
+        p0 = a == 0;
+        p1 = a == 1;
+        p2 = a == 2;
         split = splits && df_le(rmax, tm);
         // axes crossing together with the earliest one (relative tie 1e-12): a diagonal step
         const float tol = 1e-12f * tm.hi;
-        m0 = df_diff(W.t[0], tm) <= tol;
-        m1 = df_diff(W.t[1], tm) <= tol;
-        m2 = df_diff(W.t[2], tm) <= tol;
+        const bool m0 = df_diff(W.t[0], tm) <= tol;
+        const bool m1 = df_diff(W.t[1], tm) <= tol;
+        const bool m2 = df_diff(W.t[2], tm) <= tol;
         nidx = W.idx + (m0 ? W.ss[0] : 0) + (m1 ? W.ss[1] : 0) + (m2 ? W.ss[2] : 0);
-        out = (m0 && W.rem[0] == 0) || (m1 && W.rem[1] == 0) || (m2 && W.rem[2] == 0);
         // tied axes other than a advance here; axis a advances with the common path below
         if (m0 && a != 0) W.t[0] = df_add(W.t[0], W.d[0]);
         if (m1 && a != 1) W.t[1] = df_add(W.t[1], W.d[1]);
         if (m2 && a != 2) W.t[2] = df_add(W.t[2], W.d[2]);
     }
     o.ds = df_diff(split ? rmax : tm, W.tc);
-    const bool go = !split && !out;
-    const Cell ncell = go ? load_cell(cells + nidx) : cell_zero<Cell>();  // prefetch
+    // prefetch of the next cell: from a cell inside the grid every crossing (also a diagonal
+    // one) lands inside the padded layout
+    const Cell ncell = out ? cell_zero<Cell>() : load_cell(cells + nidx);
     // deposit in the current cell (segments of length <= 0 deposit nothing)
-    const bool seg = o.ds > 0.f;
+    const bool seg = !out && o.ds > 0.f;
     const float ds = seg ? o.ds : 0.f;
     const float x = chi_of(W.cell) * ds;
-    o.cell = seg ? W.idx : -1;
+    o.cell = W.idx;
+    o.seg = seg;
     o.Lin = W.L;
     o.dtau = x;
     if (!kCountOnly) {
@@ -371,7 +416,14 @@ __device__ __forceinline__ StepOut walk_step(WalkT<Cell>& W, bool splits, df rma
         o.phi = ph;
         o.G = W.L * ds * ph;
         o.dL = W.L * x * ph;
-        W.L = W.L - o.dL;
+        // L - dL, and its rounding error (Fast2Sum, dL <= L) kept for the photon ledger:
+        // where a cell is nearly transparent dL falls below half an ulp of L, so the
+        // deposited dL never leaves L. The deposits keep using L itself, whose relative
+        // accuracy survives strong attenuation (L + Lc carries the absolute error of all
+        // deposits instead); only the tallies of retired rays take L + Lc.
+        const float Lnew = __fsub_rn(W.L, o.dL);
+        W.Lc = __fadd_rn(W.Lc, __fsub_rn(__fsub_rn(W.L, Lnew), o.dL));
+        W.L = Lnew;
     } else {
         o.phi = 1.f;
         o.G = 0.f;
@@ -384,23 +436,24 @@ __device__ __forceinline__ StepOut walk_step(WalkT<Cell>& W, bool splits, df rma
         // the larger one) passes tau_max
         const float xn = W.cell.y * ds;
         o.dLn = W.Ln * xn * phi_of(xn);
-        W.Ln = W.Ln - o.dLn;
+        const float Lnnew = __fsub_rn(W.Ln, o.dLn);
+        W.Lnc = __fadd_rn(W.Lnc, __fsub_rn(__fsub_rn(W.Ln, Lnnew), o.dLn));
+        W.Ln = Lnnew;
         W.taun += xn;
         drop = seg && W.taun > tau_max;
     } else {
         o.dLn = 0.f;
         drop = seg && W.tau > tau_max;
     }
-    o.ev = drop ? EV_DROP : (split ? EV_SPLIT : (out ? EV_EXIT : EV_NONE));
+    o.end = out || drop || split;
+    o.ev = out ? EV_EXIT : (drop ? EV_DROP : (split ? EV_SPLIT : EV_NONE));
     // advance: the earliest axis by select, further tied axes on the side path
-    const df dsel = df_sel(a == 0, W.d[0], df_sel(a == 1, W.d[1], W.d[2]));
+    const df dsel = {p0 ? W.d[0].hi : (p1 ? W.d[1].hi : W.d[2].hi),
+                     p0 ? W.d[0].lo : (p1 ? W.d[1].lo : W.d[2].lo)};
     const df tn = df_add(tm, dsel);
-    W.t[0] = df_sel(a == 0, tn, W.t[0]);
-    W.t[1] = df_sel(a == 1, tn, W.t[1]);
-    W.t[2] = df_sel(a == 2, tn, W.t[2]);
-    W.rem[0] -= m0 ? 1 : 0;
-    W.rem[1] -= m1 ? 1 : 0;
-    W.rem[2] -= m2 ? 1 : 0;
+    W.t[0] = df_sel(p0, tn, W.t[0]);
+    W.t[1] = df_sel(p1, tn, W.t[1]);
+    W.t[2] = df_sel(p2, tn, W.t[2]);
     W.tc = tm;
     W.idx = nidx;
     W.cell = ncell;
@@ -445,6 +498,10 @@ __device__ __forceinline__ void deposit_merged(float4* __restrict__ acc, int cel
 __device__ __forceinline__ void deposit(float4* __restrict__ acc, int cell, float4 v)
 {
     if (cell >= 0) red_v4(acc + cell, v);
+}
+__device__ __forceinline__ void deposit_if(float4* __restrict__ acc, bool dep, int cell, float4 v)
+{
+    if (dep) red_v4(acc + cell, v);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -536,9 +593,11 @@ __device__ __forceinline__ int ray_begin(const TraceArgs& A, const LevelInfo& LV
     const df inv[3] = {{e1.z, e2.y}, {e1.w, e2.z}, {e2.x, e2.w}};
     const bool inside = walk_start(W, A.nx, A.ny, A.nz, u, n, inv, LV.r0);
     W.L = L0;
+    W.Lc = 0.f;
     W.tau = tau0;
     if constexpr (TwoBin<Cell>::value) {
         W.Ln = (l == A.level0) ? __ldg(A.srcLn + s) : __ldcg(B.Ln + i);
+        W.Lnc = 0.f;
         W.taun = (l == A.level0) ? 0.f : __ldcg(B.taun + i);
     }
     W.cell = inside ? load_cell(cells + W.idx) : cell_zero<Cell>();

@@ -36,6 +36,7 @@ struct art_grid {
     cudaStream_t stream = nullptr;
     int n[3] = {0, 0, 0};
     long long ncell = 0;
+    long long npad = 0;          // cells of the padded layout (sentinel ring around the grid)
     double lo[3] = {0, 0, 0};
     double dx = 1.0;
     const float* nH0 = nullptr;  // borrowed
@@ -43,7 +44,7 @@ struct art_grid {
     std::vector<double> pos, L;  // host copies of the sources
     std::vector<double> Ln;      // non-ionizing luminosities (two-bin traces)
     bool two_bin = false;
-    float2* d_chi2 = nullptr;    // {chi_i, chi_n} per cell length (two-bin traces)
+    float2* d_chi2 = nullptr;    // {chi_i, chi_n} per cell length (two-bin traces, padded)
     float* d_srcLn = nullptr;    // base-ray non-ionizing luminosity per source
     size_t srcLn_cap = 0;
     std::vector<float> h_Ln_stage;
@@ -52,9 +53,9 @@ struct art_grid {
     std::vector<int> src_lmax;
 
     // device buffers owned by the grid
-    float* d_chi = nullptr;      // opacity per cell length
-    float* d_chiH = nullptr;     // its neutral-H part (adjoint)
-    float4* d_acc = nullptr;     // per-cell accumulator
+    float* d_chi = nullptr;      // opacity per cell length (padded layout)
+    float4* d_acc = nullptr;     // per-cell accumulator (padded layout); the reverse sweep
+                                 // sums its gradient in the first npad floats
     art::SrcDev* d_src = nullptr;
     size_t src_cap = 0;
     art::LevelInfo* d_levels = nullptr;
@@ -74,7 +75,7 @@ struct art_grid {
 
     // adjoint: source luminosities and a dL buffer for callers that pass none
     float* d_srcL = nullptr;
-    float4* d_rec = nullptr;     // per-cell {chi, chi_H, w, 0} of the reverse sweep
+    float4* d_rec = nullptr;     // per-cell {chi, chi_H, w, 0} of the reverse sweep (padded)
     art::CellF* d_recf = nullptr;  // the same with the force weight (loss with a force term)
     double* d_dL_scratch = nullptr;
     size_t srcL_cap = 0;
@@ -102,6 +103,9 @@ struct art_grid {
 
 namespace art {
 int check_params(const art_params* p);
+int ensure_directions(art_grid* g, const art_params* p, int lfrom, int lto);
+int run_opacity(art_grid* g, const art_params* p, bool two_bin);
+double rmax_cells(double m_ray, int level);
 int prepare_trace(art_grid* g, const art_params* p, bool adjoint);
 TraceArgs make_args(art_grid* g, const art_params* p);
 int finish_stats(art_grid* g, art_stats* out);

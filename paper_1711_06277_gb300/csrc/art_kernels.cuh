@@ -109,24 +109,30 @@ __global__ void k_directions(int level, unsigned long long npix, double r0, doub
     dir[3 * p + 2] = make_float4(ih[2], il[0], il[1], il[2]);
 }
 
-// chi per cell length (dx) in FP32 from the density fields; flags bad densities.
-__global__ void k_opacity(long long ncell, const float* __restrict__ nH0,
+// chi per cell length (dx) in FP32 from the density fields, in the padded layout with the
+// sentinel ring; flags bad densities.
+__global__ void k_opacity(int nx, int ny, int nz, const float* __restrict__ nH0,
                           const float* __restrict__ nH, double sH_dx, double sd_dx,
-                          float* __restrict__ chi, float* __restrict__ chiH,
-                          float2* __restrict__ chi2, DevStats* __restrict__ st)
+                          float* __restrict__ chi, float2* __restrict__ chi2,
+                          DevStats* __restrict__ st)
 {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long step = (long long)gridDim.x * blockDim.x;
+    const unsigned npad = (unsigned)(nx + 2) * (unsigned)(ny + 2) * (unsigned)(nz + 2);
+    const unsigned step = gridDim.x * blockDim.x;
     bool bad = false;
-    for (; i < ncell; i += step) {
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < npad; q += step) {
+        unsigned i;
+        if (!unpad(q, nx, ny, nz, i)) {
+            chi[q] = kSentinel;
+            if (chi2) chi2[q] = make_float2(kSentinel, 0.f);
+            continue;
+        }
         float a = nH0[i];
         float b = nH ? nH[i] : 0.f;
         bad = bad || !(a >= 0.f) || !(b >= 0.f) || isinf(a) || isinf(b);
         double h = (double)a * sH_dx;
         const double dust = (double)b * sd_dx;
-        chi[i] = __double2float_rn(h + dust);
-        if (chiH) chiH[i] = __double2float_rn(h);
-        if (chi2) chi2[i] = make_float2(__double2float_rn(h + dust), __double2float_rn(dust));
+        chi[q] = __double2float_rn(h + dust);
+        if (chi2) chi2[q] = make_float2(__double2float_rn(h + dust), __double2float_rn(dust));
     }
     if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicCAS(&st->error, 0, -1);
 }
@@ -210,7 +216,7 @@ __device__ void run_rays(const TraceArgs& A, const Cell* cells, int l,
                     } else {
                         if (st == 0) {  // starts outside the grid: escapes with its full L
                             atomicAdd(&T.escaped, (double)L0);
-                            if constexpr (two) atomicAdd(&T.escaped_n, (double)W.Ln);
+                            if constexpr (two) atomicAdd(&T.escaped_n, (double)W.Ln + (double)W.Lnc);
                             atomicAdd(&T.destroy, LV.destroy_w);
                             ++nrays;
                         }
@@ -228,7 +234,8 @@ __device__ void run_rays(const TraceArgs& A, const Cell* cells, int l,
 
 #pragma unroll 1
         for (int k = 0; k < 64; ++k) {  // steps between refill checks (measured: 64 > 32 > 16 > 8)
-            int cell = -1;
+            bool dep = false;
+            int cell = 0;
             float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
             if (active) {
                 // a ray ends at a radius when it can split or (kCut) at the d_max cutoff
@@ -238,11 +245,12 @@ __device__ void run_rays(const TraceArgs& A, const Cell* cells, int l,
                                          A.tau_max);
                 else
                     o = walk_step<false>(W, splits, lv_rmax, cells, A.tau_max);
-                cell = o.cell;  // < 0 when the segment had no length
+                dep = o.seg;  // segments without length deposit nothing
+                cell = o.cell;
                 const float dm = two ? o.dL + o.dLn : o.dL;  // momentum of both bins
                 dv = make_float4(o.G, dm * W.n[0], dm * W.n[1], dm * W.n[2]);
-                ncross += o.cell >= 0 ? 1u : 0u;
-                if (o.ev != EV_NONE) {
+                ncross += o.seg ? 1u : 0u;
+                if (o.end) {
                     active = false;
                     const unsigned long long c4 = 4ull * (slot - b32);
                     if (o.ev == EV_SPLIT && (!kCut || splits_at_end(splits, LV.rmax, A.dmax))) {
@@ -263,21 +271,28 @@ __device__ void run_rays(const TraceArgs& A, const Cell* cells, int l,
                         } else {
                             atomicCAS(&A.stats->error, 0, -3);  // ART_EQUEUE_OVERFLOW
                         }
+                        // the split ray's ledger residual: its children start from L itself
+                        if (W.Lc != 0.f) atomicAdd(&T.escaped, (double)W.Lc);
+                        if constexpr (two) {
+                            if (W.Lnc != 0.f) atomicAdd(&T.escaped_n, (double)W.Lnc);
+                        }
                     } else {
                         // leaving the box or cut at d_max: escaped; tau > tau_max: dropped
-                        if (o.ev != EV_DROP) atomicAdd(&T.escaped, (double)W.L);
-                        else atomicAdd(&T.dropped, (double)W.L);
+                        const double Lend = (double)W.L + (double)W.Lc;
+                        if (o.ev != EV_DROP) atomicAdd(&T.escaped, Lend);
+                        else atomicAdd(&T.dropped, Lend);
                         if constexpr (two) {
-                            if (o.ev != EV_DROP) atomicAdd(&T.escaped_n, (double)W.Ln);
-                            else atomicAdd(&T.dropped_n, (double)W.Ln);
+                            const double Lnend = (double)W.Ln + (double)W.Lnc;
+                            if (o.ev != EV_DROP) atomicAdd(&T.escaped_n, Lnend);
+                            else atomicAdd(&T.dropped_n, Lnend);
                         }
                         atomicAdd(&T.destroy, LV.destroy_w);
                         if (has_next) write_holes(C, c4);
                     }
                 }
             }
-            if (base && __any_sync(kFull, first)) deposit_merged(A.acc, cell, dv);
-            else deposit(A.acc, cell, dv);
+            if (base && __any_sync(kFull, first)) deposit_merged(A.acc, dep ? cell : -1, dv);
+            else deposit_if(A.acc, dep, cell, dv);
             first = false;
         }
     }
@@ -286,8 +301,19 @@ __device__ void run_rays(const TraceArgs& A, const Cell* cells, int l,
 }
 
 // Plain schedule: all slots of level l (one source's front).
+// Launch bounds of the trace kernels: at most ART_TRACE_MAX_THREADS threads per block and
+// ART_TRACE_MIN_BLOCKS resident blocks per SM, which caps the registers per thread at
+// 65536 / (threads x blocks).
+#ifndef ART_TRACE_MAX_THREADS
+#define ART_TRACE_MAX_THREADS 512
+#endif
+#ifndef ART_TRACE_MIN_BLOCKS
+#define ART_TRACE_MIN_BLOCKS 2
+#endif
+constexpr int kTraceMaxThreads = ART_TRACE_MAX_THREADS;
+
 template <class Cell, bool kCut>
-__global__ void __launch_bounds__(512, 2) k_trace_level(const __grid_constant__ TraceArgs A, int l)
+__global__ void __launch_bounds__(ART_TRACE_MAX_THREADS, ART_TRACE_MIN_BLOCKS) k_trace_level(const __grid_constant__ TraceArgs A, int l)
 {
     tally_init();
     Tally& T = tally_slots()[threadIdx.x >> 5];
@@ -308,7 +334,7 @@ __global__ void k_reset_counts(Sched* sc)
 
 // Persistent schedule: all sources, all levels, one cooperative launch.
 template <class Cell, bool kCut>
-__global__ void __launch_bounds__(512, 2) k_trace_persistent(const __grid_constant__ TraceArgs A)
+__global__ void __launch_bounds__(ART_TRACE_MAX_THREADS, ART_TRACE_MIN_BLOCKS) k_trace_persistent(const __grid_constant__ TraceArgs A)
 {
     tally_init();
     Tally& T = tally_slots()[threadIdx.x >> 5];
@@ -328,6 +354,10 @@ __global__ void __launch_bounds__(512, 2) k_trace_persistent(const __grid_consta
                 unsigned long long have = min(cnt[l], A.buf[l].cap);
                 unsigned long long take = have;
                 if (l < A.lmax_glob) take = min(have, A.buf[l + 1].cap / 4);
+                if (take == 0) {  // a phase must consume rays, or the schedule never ends
+                    atomicCAS(&A.stats->error, 0, -8);  // ART_EINTERNAL
+                    take = have;
+                }
                 sc->phase_level = l;
                 sc->phase_begin = have - take;
                 sc->phase_end = have;
@@ -352,20 +382,21 @@ __global__ void __launch_bounds__(512, 2) k_trace_persistent(const __grid_consta
     tally_flush(A.stats);
 }
 
-// Gamma, force and energy from the accumulator (SoA outputs).
-__global__ void k_finalize(long long ncell, const float4* __restrict__ acc, float gscale,
+// Gamma, force and energy from the accumulator (padded layout) into the caller's SoA
+// outputs (nx*ny*nz layout).
+__global__ void k_finalize(int nx, int ny, int nz, const float4* __restrict__ acc, float gscale,
                            float fscale, float escale, float* __restrict__ gamma,
                            float* __restrict__ force, float* __restrict__ energy)
 {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long step = (long long)gridDim.x * blockDim.x;
-    for (; i < ncell; i += step) {
-        float4 a = __ldcs(acc + i);
+    const unsigned ncell = (unsigned)nx * (unsigned)ny * (unsigned)nz;
+    const unsigned step = gridDim.x * blockDim.x;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += step) {
+        const float4 a = __ldcs(acc + pad_of(i, nx, ny));
         gamma[i] = gscale * a.x;
         if (force) {
             force[i] = fscale * a.y;
-            force[ncell + i] = fscale * a.z;
-            force[2 * ncell + i] = fscale * a.w;
+            force[(size_t)ncell + i] = fscale * a.z;
+            force[2 * (size_t)ncell + i] = fscale * a.w;
         }
         if (energy) energy[i] = escale * a.x;
     }

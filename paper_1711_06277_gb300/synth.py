@@ -27,6 +27,7 @@ __all__ = [
     "cell_centre_position",
     "uniform_weights",
     "random_rotation",
+    "bubble_neutral_fraction",
 ]
 
 
@@ -96,3 +97,32 @@ def random_rotation(seed: int) -> np.ndarray:
     if np.linalg.det(q) < 0:
         q[:, 0] = -q[:, 0]
     return q
+
+
+def bubble_neutral_fraction(n: int, pos, L, r_max: float = 0.12, x_in: float = 1e-4,
+                            x_out: float = 1.0, width: float = 1.5, side: float = 1.0) -> np.ndarray:
+    """Neutral fraction with ionized bubbles around sources, shape (n, n, n), float64.
+
+    A stand-in for the neutral fraction of a grid some time after its sources switched on
+    (Sec. 3.3.1, 4): low (x_in) inside a sphere around each source, high (x_out) outside,
+    with a transition ``width`` cells thick (logistic in the distance). Bubble radii grow
+    like L^(1/3), r_max (box units) for the brightest source. Purely an input shape: no step
+    of the ray-tracing method is used to make it."""
+    pos = np.asarray(pos, dtype=np.float64).reshape(-1, 3)
+    L = np.asarray(L, dtype=np.float64).reshape(-1)
+    dx = side / n
+    ion = np.zeros((n, n, n))  # ionized share in [0, 1], the largest over the bubbles
+    radii = r_max * (L / L.max()) ** (1.0 / 3.0)
+    c = (np.arange(n) + 0.5) * dx
+    for p, r in zip(pos, radii):
+        reach = r + 6.0 * width * dx
+        lo = np.clip(np.floor((p - reach) / dx).astype(int), 0, n)
+        hi = np.clip(np.ceil((p + reach) / dx).astype(int) + 1, 0, n)
+        if np.any(hi <= lo):
+            continue
+        z, y, x = np.meshgrid(c[lo[2]:hi[2]], c[lo[1]:hi[1]], c[lo[0]:hi[0]], indexing="ij")
+        d = np.sqrt((x - p[0]) ** 2 + (y - p[1]) ** 2 + (z - p[2]) ** 2)
+        share = 1.0 / (1.0 + np.exp((d - r) / (width * dx)))
+        sub = ion[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]]
+        np.maximum(sub, share, out=sub)
+    return x_out - (x_out - x_in) * ion

@@ -80,7 +80,7 @@ def _workload(n, sigma_ln, nsrc, seed):
     return rho, synth.uniform_positions(nsrc, seed=seed), synth.power_law_luminosities(nsrc, seed=seed)
 
 
-def _subset_parity(A, nH0, pos, L, dx, sigma_H):
+def _subset_parity(A, nH0, pos, L, dx, sigma_H, net_force=False):
     dev = torch.device("cuda")
     p = A.Params(level0=4, tau_max=30.0, sigma_H=sigma_H)
     g = A.Grid(torch.from_numpy(nH0).to(dev), dx)
@@ -89,52 +89,80 @@ def _subset_parity(A, nH0, pos, L, dx, sigma_H):
     res = {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in out.items()}
     g.close()
     ref = O.trace(O.Problem(nH0=nH0, pos=pos, L=L, dx=dx, sigma_H=sigma_H, level0=4,
-                            tau_max=30.0), nthreads=os.cpu_count() or 8)
+                            tau_max=30.0), nthreads=os.cpu_count() or 8, count_hits=True)
     st = res["stats"]
-    PA.compare_field(res["gamma"], ref.gamma, what="gamma")
+    PA.compare_field(res["gamma"], ref.gamma, what="gamma", hits=ref.hits)
     chi = nH0.astype(np.float64) * sigma_H
-    PA.compare_force(res["force"], ref.force, chi * ref.energy)
+    PA.compare_force(res["force"], ref.force, chi * ref.energy, hits=ref.hits)
+    if net_force:
+        PA.compare_force_net(res["force"], ref.force, chi * ref.energy)
     assert abs(st["crossings"] - ref.crossings) <= max(0, ref.near_tie_rays) * 4
     assert abs(st["L_escaped"] - ref.escaped) <= PA.CONS * ref.L_in
     assert st["destroy"] == st["destroy_expected"]
 
 
 def test_config3_source_subset_parity(art):
+    """256^3 lognormal (sigma_ln = 2), 8 of the 64 sources."""
     n = 256
     rho, pos, L = _workload(n, 2.0, 64, seed=3)
-    _subset_parity(art, rho, pos[:4], L[:4], 1.0 / n, 10.0)
+    _subset_parity(art, rho, pos[:8], L[:8], 1.0 / n, 10.0, net_force=True)
 
 
 def test_config5_source_subset_parity(art):
+    """512^3, 8 of the 1024 sources, on the neutral density of the bench's first step
+    (x_n = 1e-3) and on a few sources of the fully neutral grid (tau_box = 10)."""
     n = 512
     rho, pos, L = _workload(n, 2.0, 1024, seed=5)
     nH = (100.0 * rho).astype(np.float32)
-    # fully neutral (tau_box = 10) for two sources, and the initial x_n = 1e-3 for one
-    _subset_parity(art, nH, pos[:2], L[:2], 1.0 / n, 0.1)
-    _subset_parity(art, (1e-3 * nH).astype(np.float32), pos[2:3], L[2:3], 1.0 / n, 0.1)
+    _subset_parity(art, (1e-3 * nH).astype(np.float32), pos[:8], L[:8], 1.0 / n, 0.1)
+    _subset_parity(art, nH, pos[8:11], L[8:11], 1.0 / n, 0.1)
 
 
-def test_config5_full_size_properties(art):
-    """All 1024 sources in the launch configuration the bench times: photon conservation,
-    the destroy counter, and additivity over two halves of the sources (which with the
-    subset parity above ties the full trace to the oracle). Each cell sums ~10^4 FP32
-    deposits here in an order that changes from run to run; additivity is checked at 2e-4,
-    the bound of such sums (observed worst cell 7.7e-5 over the 1.3e8 cells)."""
+def test_config5_subset_parity_ionized_bubbles(art):
+    """512^3, 8 of the 1024 sources on a neutral fraction with ionized bubbles around every
+    source (synth.bubble_neutral_fraction): sharp fronts and a contrast of 10^4 between
+    bubbles and neutral gas, the structure the coupled steps of the bench build up. The
+    field is a seeded input, not the GPU's own evolved field, so that no oracle input comes
+    from the CUDA path."""
     n = 512
     rho, pos, L = _workload(n, 2.0, 1024, seed=5)
-    nH0 = torch.from_numpy((1e-3 * 100.0 * rho).astype(np.float32)).cuda()
-    # the launch configuration the bench's autotuner picks for this workload
-    p = art.Params(level0=4, tau_max=30.0, sigma_H=0.1, chunk=64, block_threads=512,
-                   queue_capacity=256 << 20)
-    g = art.Grid(nH0, 1.0 / n)
-    g.add_sources(pos, L)
+    xn = synth.bubble_neutral_fraction(n, pos, L)
+    nH0 = (100.0 * rho * xn).astype(np.float32)
+    assert 0.03 < (xn < 0.5).mean() < 0.3
+    _subset_parity(art, nH0, pos[:8], L[:8], 1.0 / n, 0.1)
+
+
+def _max_deposits(nsrc, level0=4, m_ray=4.0):
+    """Bound of the deposits per cell. Beyond r_max(l0) the splitting keeps at most 4 m_ray
+    rays per unit area across a ray bundle, and a cell presents at most sqrt(3) of area, so
+    a source sends at most 4 m_ray sqrt(3) rays through a cell; a source's own cell takes
+    its 12 4^l0 base rays (a cell holds at most two of the sources here)."""
+    return nsrc * 4 * m_ray * math.sqrt(3.0) + 2 * 12 * 4 ** level0
+
+
+def _additivity_tol(nsrc, cells):
+    """Bound of |full - (half_1 + half_2)| / full for per-cell FP32 sums: the full sum and
+    the two half sums each obey parity.sum_tol of their deposit counts."""
+    n_full = _max_deposits(nsrc)
+    t_full = float(PA.sum_tol(np.array([n_full]), cells)[0])
+    t_half = float(PA.sum_tol(np.array([n_full / 2]), cells)[0])
+    return t_full + t_half
+
+
+def _full_size_checks(art, g, p, pos, L, nH0):
     full = g.trace(p, force=False, energy=True)
     st = full["stats"]
     assert st["status"] == 0 and st["destroy"] == st["destroy_expected"]
+    n = nH0.shape[0]
     G = full["energy"].double() * (1.0 / n) ** 3
     chi = nH0.double() * 0.1
     absorbed = float((chi * G).sum())
-    assert abs(absorbed + st["L_escaped"] + st["L_dropped"] - st["L_in"]) <= PA.CONS * st["L_in"]
+    # the absorbed light summed on the host from the per-cell FP32 accumulators carries
+    # their summation error, at most sum_tol of the deposit bound in every cell; the
+    # trace's own FP64 tallies meet the 1e-6 bar against the oracle in the subset tests
+    tol = max(PA.CONS, absorbed / st["L_in"] *
+              float(PA.sum_tol(np.array([_max_deposits(1024)]), n ** 3)[0]))
+    assert abs(absorbed + st["L_escaped"] + st["L_dropped"] - st["L_in"]) <= tol * st["L_in"]
     gam_full = full["gamma"].double().cpu().numpy()
     del full, G, chi
     halves, counts = [], []
@@ -144,9 +172,39 @@ def test_config5_full_size_properties(art):
         h = g.trace(p, force=False)
         halves.append(h["gamma"].double().cpu().numpy())
         counts.append(h["stats"])
-    g.close()
+    g.clear_sources()
+    g.add_sources(pos, L)
     # every ray's path depends only on its own source: integer counts add exactly
     assert st["crossings"] == counts[0]["crossings"] + counts[1]["crossings"]
     assert st["rays_per_level"] == [a + b for a, b in zip(counts[0]["rays_per_level"],
                                                           counts[1]["rays_per_level"])]
-    PA.compare_field(gam_full, halves[0] + halves[1], rel=2e-4, what="additivity")
+    PA.compare_field(gam_full, halves[0] + halves[1], rel=_additivity_tol(1024, n ** 3),
+                     what="additivity")
+
+
+def test_config5_full_size_properties(art):
+    """All 1024 sources in the launch configuration the bench times, on the first step's
+    field and after three coupled steps (trace + Eq. e:xn3): photon conservation, the
+    destroy counter, and additivity over two halves of the sources (which with the subset
+    parity above ties the full trace to the oracle) within the FP32-sum bound of the
+    cells' deposit counts."""
+    n = 512
+    rho, pos, L = _workload(n, 2.0, 1024, seed=5)
+    nH = torch.from_numpy((100.0 * rho).astype(np.float32)).cuda()
+    xn = torch.full_like(nH, 1e-3)
+    nH0 = (xn * nH).contiguous()
+    # the launch configuration the bench's autotuner picks for this workload
+    p = art.Params(level0=4, tau_max=30.0, sigma_H=0.1, chunk=64, block_threads=512,
+                   queue_capacity=256 << 20)
+    g = art.Grid(nH0, 1.0 / n)
+    g.add_sources(pos, L)
+    _full_size_checks(art, g, p, pos, L, nH0)
+    gam = torch.empty_like(nH)
+    alpha = 2e-4
+    for _ in range(3):
+        g.trace(p, force=False, stats=False, out={"gamma": gam})
+        art.xn_update(gam, nH, xn, alpha, 0.1 / (alpha * 100.0), nH0_out=nH0)
+    ionized = float((xn < 0.5).float().mean())
+    assert ionized > 0.01
+    _full_size_checks(art, g, p, pos, L, nH0)
+    g.close()

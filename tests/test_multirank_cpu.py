@@ -1,5 +1,5 @@
-"""The N-replica timing path of bench.py on two CPU ranks (gloo): max of the ranks' times,
-sum of their crossings, no other exchange."""
+"""The whole-job timing of bench.py under torchrun on two CPU ranks (gloo): the slowest
+rank's time and the sum of the ranks' crossings."""
 import os
 import socket
 
@@ -30,7 +30,7 @@ def _worker(rank, world, port, out):
 
 def test_two_rank_reduction():
     world, port = 2, _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
