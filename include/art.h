@@ -187,7 +187,9 @@ int art_get_stats(art_grid* g, art_stats* h_stats);
  * Split points and tau_max retirement are held fixed. A force term doubles the per-step
  * gather (32-byte cell records, 32 B x ncell of library memory). One-bin traces only
  * (ART_EINVAL with a second bin). Same parameters and status rules as art_trace; h_stats
- * as in art_trace. */
+ * as in art_trace, with crossings, rays per level and the destroy counter; its photon
+ * tallies (escaped, dropped) are zero, because the reverse sweep walks rays of unit
+ * source luminosity. */
 int art_trace_backward(art_grid* g, const art_params* p, const float* d_w, const float* d_v,
                        float* d_dlog_nH0, double* d_dL, art_stats* h_stats);
 

@@ -142,11 +142,12 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
     df rmax = LV.rmax;     // radius where the ray of level lv ends (split or cutoff)
     bool splits = false;
     unsigned ncross = 0, nrays = 0;
-    // Every step crosses at least one face, so a walk inside the grid takes at most
-    // nx + ny + nz steps plus the one into the sentinel ring. A walk that outlives that
-    // bound is abandoned with ART_EINTERNAL, so the kernel always ends.
-    const int step_bound = A.nx + A.ny + A.nz + 4;
-    int steps_left = step_bound;
+    // Every step crosses at least one face and the sentinel ring ends every walk that
+    // leaves the grid, so walks end by construction. As a safety net the warp counts its
+    // rounds of steps (ART_ADJ_STEPS each) and gives up past a bound far beyond any phase
+    // (ART_EINTERNAL), so the kernel always ends.
+    unsigned rounds = 0;
+    unsigned nretired = 0;  // rays retired here (weight destroy_w each, summed at the end)
 
     // Completion of the ray in `slot` at level lv (pass 2 done, or a ray without segments):
     // dL, the parent's sum, and possibly the parent's pass 2 in this lane.
@@ -214,8 +215,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
                     } else {
                         if (has_next) write_holes(C, 4ull * (slot - b32));
                         if (st == 0) {  // starts outside the grid: a leaf with zero sums
-                            atomicAdd(&T.escaped, (double)L0);
-                            atomicAdd(&T.destroy, LV.destroy_w);
+                            ++nretired;
                             ++nrays;
                             own = {0.f, 0.f};
                             total = 0.f;
@@ -232,6 +232,10 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
             continue;
         }
 
+        if (++rounds > (1u << 28)) {  // warp-uniform: no phase comes near this
+            if (lane == 0) atomicCAS(&A.stats->error, 0, -8);  // ART_EINTERNAL
+            break;
+        }
 #pragma unroll 1
         for (int k = 0; k < ART_ADJ_STEPS; ++k) {
             if (mode != 0) {
@@ -241,16 +245,6 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
                 const float q = force_weight(W.cell, W.n, A.fscale);
                 // a ray ends at a radius (rmax) when it can split or (kCut) at the cutoff
                 const StepOut o = walk_step<false, true>(W, kCut || splits, rmax, recs, A.tau_max);
-                if (--steps_left < 0 && !o.end) {
-                    atomicCAS(&A.stats->error, 0, -8);  // ART_EINTERNAL: abandon the walk
-                    // a pass-1 ray leaves no children (its four slots marked empty); an
-                    // abandoned pass 2 never counts its parent down
-                    if (mode == 1 && has_next) write_holes(C, 4ull * (slot - b32));
-                    mode = 0;
-                    steps_left = step_bound;
-                    continue;
-                }
-                if (o.end) steps_left = step_bound;  // the next walk of this lane starts
                 // this segment's loss: w k G, plus q dL with a force term
                 const float g = fmaf(q, o.dL, wv * gs * o.G);
                 if (mode == 1) {
@@ -287,10 +281,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
                             }
                             mode = 0;
                         } else {
-                            const double Lend = (double)W.L + (double)W.Lc;
-                            if (o.ev != EV_DROP) atomicAdd(&T.escaped, Lend);  // exit or cut
-                            else atomicAdd(&T.dropped, Lend);
-                            atomicAdd(&T.destroy, LV.destroy_w);
+                            ++nretired;
                             if (has_next) write_holes(C, c4);
                             // a leaf: pass 2 right away
                             total = own.hi + own.lo;
@@ -317,6 +308,10 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
     }
     tally_crossings(T, ncross);
     count_rays(A.stats, l, nrays);
+    // the destroy counter: rays retired at this phase's level, weight 4^(l_max - l)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) nretired += __shfl_down_sync(kFull, nretired, off);
+    if (lane == 0 && nretired > 0) atomicAdd(&T.destroy, (unsigned long long)nretired * LV.destroy_w);
 }
 
 template <class Cell, bool kCut>

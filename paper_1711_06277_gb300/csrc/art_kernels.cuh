@@ -163,6 +163,15 @@ template <class Cell> __device__ __forceinline__ const Cell* cells_of(const Trac
 template <> __device__ __forceinline__ const float* cells_of<float>(const TraceArgs& A) { return A.chi; }
 template <> __device__ __forceinline__ const float2* cells_of<float2>(const TraceArgs& A) { return A.chi2; }
 
+// Idle lanes of a warp before it refills them from its chunk, and steps between refill
+// checks (measured: 16 lanes > 18, 14 > 12 > 10; 64 steps > 32 > 16 > 8).
+#ifndef ART_FWD_IDLE
+#define ART_FWD_IDLE 16
+#endif
+#ifndef ART_FWD_STEPS
+#define ART_FWD_STEPS 64
+#endif
+
 template <class Cell, bool kCut>
 __device__ void run_rays(const TraceArgs& A, const Cell* cells, int l,
                          unsigned long long* cursor, unsigned long long begin,
@@ -194,7 +203,7 @@ __device__ void run_rays(const TraceArgs& A, const Cell* cells, int l,
     for (;;) {
         // refill idle lanes from the warp's chunk, fetching chunks as needed
         unsigned need = __ballot_sync(kFull, !active);
-        if (__popc(need) >= 16 || need == kFull) {  // measured: 16 > 18, 14 > 12 > 10
+        if (__popc(need) >= ART_FWD_IDLE || need == kFull) {
             while (need && more) {
                 if (wnext >= wend) {
                     unsigned long long b = 0;
@@ -233,7 +242,7 @@ __device__ void run_rays(const TraceArgs& A, const Cell* cells, int l,
         }
 
 #pragma unroll 1
-        for (int k = 0; k < 64; ++k) {  // steps between refill checks (measured: 64 > 32 > 16 > 8)
+        for (int k = 0; k < ART_FWD_STEPS; ++k) {
             bool dep = false;
             int cell = 0;
             float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
