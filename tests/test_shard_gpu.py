@@ -126,3 +126,65 @@ def test_sharded_trace_single_rank_and_backward(art):
                                            level0=3, tau_max=30.0), w.cpu().numpy(), nthreads=8)
     PA.compare_field(grad.cpu().numpy(), rg, what="grad")
     np.testing.assert_allclose(dL.cpu().numpy(), rdL, rtol=PA.REL)
+
+
+def _two_rank_worker(rank, world, port, out):
+    """One rank of a two-process ShardedTrace on the same GPU: the ranks' kernels never wait
+    on each other; their only exchange is the gloo all-reduce between launches."""
+    import os
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_1711_06277_gb300 import art as A, shard
+    n = 40
+    rho = synth.lognormal_field(n, 1.5, seed=45).astype(np.float32)
+    pos = synth.uniform_positions(5, seed=45)
+    L = synth.power_law_luminosities(5, seed=45)
+    w = torch.from_numpy(synth.uniform_weights(n, seed=45).astype(np.float32)).cuda()
+    p = A.Params(level0=3, tau_max=30.0, sigma_H=8.0)
+    st = shard.ShardedTrace(torch.from_numpy(rho).cuda(), 1.0 / n, pos, L, p)
+    res = st.trace()
+    grad, dL = st.backward(w)
+    out[rank] = dict(gamma=res["gamma"].cpu().numpy(), force=res["force"].cpu().numpy(),
+                     stats=res["stats"], mine=st.mine.tolist(), load=st.load.tolist(),
+                     grad=grad.cpu().numpy(), dL=dL.cpu().numpy())
+    st.close()
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_sharded_trace_two_processes_on_one_gpu(art):
+    """The whole sharded path with two ranks: rank 0's work estimate, the partition, each
+    rank's trace of its sources, the all-reduce of gamma and force and of the reverse
+    sweep; both ranks end with the whole problem's fields, which match the oracle."""
+    import socket
+    import torch.multiprocessing as mp
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        mp.spawn(_two_rank_worker, args=(2, port, out), nprocs=2, join=True)
+        res = dict(out)
+    n = 40
+    rho = synth.lognormal_field(n, 1.5, seed=45).astype(np.float32)
+    pos = synth.uniform_positions(5, seed=45)
+    L = synth.power_law_luminosities(5, seed=45)
+    w = synth.uniform_weights(n, seed=45).astype(np.float32)
+    prob = O.Problem(nH0=rho, pos=pos, L=L, dx=1.0 / n, sigma_H=8.0, level0=3, tau_max=30.0)
+    ref = O.trace(prob, nthreads=8, count_hits=True)
+    rg, rdL, _ = O.trace_adjoint(prob, w, nthreads=8)
+    assert sorted(res[0]["mine"] + res[1]["mine"]) == list(range(5))
+    assert res[0]["mine"] and res[1]["mine"]
+    chi = rho.astype(np.float64) * 8.0
+    for r in (0, 1):
+        PA.compare_field(res[r]["gamma"], ref.gamma, what=f"rank {r} gamma", hits=ref.hits)
+        PA.compare_force(res[r]["force"], ref.force, chi * ref.energy, hits=ref.hits)
+        # exact unless the oracle flags near-tie rays (faces within 1e-5 of a cell)
+        assert abs(res[r]["stats"]["crossings"] - ref.crossings) <= 4 * ref.near_tie_rays
+        assert abs(res[r]["stats"]["L_escaped"] - ref.escaped) <= PA.CONS * ref.L_in
+        PA.compare_field(res[r]["grad"], rg, what=f"rank {r} grad")
+        np.testing.assert_allclose(res[r]["dL"], rdL, rtol=PA.REL)
+    np.testing.assert_array_equal(res[0]["gamma"], res[1]["gamma"])
