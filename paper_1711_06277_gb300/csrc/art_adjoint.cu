@@ -78,7 +78,9 @@ __device__ __forceinline__ void red_f32(float* p, float v)
 // segment: q = (v . n) / dV, so that the segment adds q dL to the loss (0 without a force term).
 __device__ __forceinline__ float4 rec_main(const float4& c) { return c; }
 __device__ __forceinline__ float4 rec_main(const CellF& c) { return c.a; }
+__device__ __forceinline__ float4 rec_main(const CellW& c) { return make_float4(c.chi, c.chi, c.w, 0.f); }
 __device__ __forceinline__ float force_weight(const float4&, const float*, float) { return 0.f; }
+__device__ __forceinline__ float force_weight(const CellW&, const float*, float) { return 0.f; }
 __device__ __forceinline__ float force_weight(const CellF& c, const float* n, float fs)
 {
     return fs * fmaf(c.b.x, n[0], fmaf(c.b.y, n[1], c.b.z * n[2]));
@@ -86,6 +88,7 @@ __device__ __forceinline__ float force_weight(const CellF& c, const float* n, fl
 template <class Cell> __device__ __forceinline__ const Cell* recs_of(const TraceArgs& A);
 template <> __device__ __forceinline__ const float4* recs_of<float4>(const TraceArgs& A) { return A.rec; }
 template <> __device__ __forceinline__ const CellF* recs_of<CellF>(const TraceArgs& A) { return A.recf; }
+template <> __device__ __forceinline__ const CellW* recs_of<CellW>(const TraceArgs& A) { return A.recw; }
 
 // Idle lanes of a warp before it refills them from the queue, and steps between refill
 // checks (measured on the 128^3 / 16-source case).
@@ -410,6 +413,23 @@ __global__ void k_pack_cells_f(int nx, int ny, int nz, const float* __restrict__
     }
 }
 
+// The 8-byte record {chi, w} of a sweep without dust and force term (sentinel {-1, 0}).
+__global__ void k_pack_cells_w(int nx, int ny, int nz, const float* __restrict__ nH0,
+                               double sH_dx, const float* __restrict__ w,
+                               CellW* __restrict__ rec)
+{
+    const unsigned npad = (unsigned)(nx + 2) * (unsigned)(ny + 2) * (unsigned)(nz + 2);
+    const unsigned step = gridDim.x * blockDim.x;
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < npad; q += step) {
+        unsigned i;
+        if (!unpad(q, nx, ny, nz, i)) {
+            rec[q] = CellW{kSentinel, 0.f};
+            continue;
+        }
+        rec[q] = CellW{__double2float_rn((double)nH0[i] * sH_dx), w ? w[i] : 0.f};
+    }
+}
+
 // Gradient per cell from the padded scratch it was summed in, into the caller's layout.
 __global__ void k_unpad_grad(int nx, int ny, int nz, const float* __restrict__ src,
                              float* __restrict__ dst)
@@ -490,7 +510,13 @@ extern "C" int art_trace_backward(art_grid* g, const art_params* p, const float*
     const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
     const double sH_dx = p->sigma_H * g->dx;
     const double sd_dx = g->nH ? p->sigma_d * g->dx : 0.0;
-    if (d_v) {
+    // without dust the neutral-H opacity is the opacity: an 8-byte record serves
+    const bool light = !d_v && sd_dx == 0.0;
+    if (light) {
+        if (!g->d_recw && (rc = status_of(cudaMalloc((void**)&g->d_recw, sizeof(CellW) * g->npad))))
+            return rc;
+        k_pack_cells_w<<<pack_blocks, 256, 0, st>>>(nx, ny, nz, g->nH0, sH_dx, d_w, g->d_recw);
+    } else if (d_v) {
         if (!g->d_recf && (rc = status_of(cudaMalloc((void**)&g->d_recf, sizeof(CellF) * g->npad))))
             return rc;
         k_pack_cells_f<<<pack_blocks, 256, 0, st>>>(nx, ny, nz, g->nH0, g->nH, sH_dx, sd_dx, d_w,
@@ -505,6 +531,7 @@ extern "C" int art_trace_backward(art_grid* g, const art_params* p, const float*
     TraceArgs A = make_args(g, p);
     A.rec = g->d_rec;
     A.recf = d_v ? g->d_recf : nullptr;
+    A.recw = light ? g->d_recw : nullptr;
     A.w = d_w;
     A.grad = grad_pad;
     A.dL = dL;
@@ -516,8 +543,9 @@ extern "C" int art_trace_backward(art_grid* g, const art_params* p, const float*
     const int threads = p->block_threads > 0 && p->block_threads < 256 ? p->block_threads : 256;
     const bool cut = p->d_max > 0.0;
     void (*kern)(TraceArgs) =
-        d_v ? (cut ? k_backward_persistent<CellF, true> : k_backward_persistent<CellF, false>)
-            : (cut ? k_backward_persistent<float4, true> : k_backward_persistent<float4, false>);
+        light ? (cut ? k_backward_persistent<CellW, true> : k_backward_persistent<CellW, false>)
+        : d_v ? (cut ? k_backward_persistent<CellF, true> : k_backward_persistent<CellF, false>)
+              : (cut ? k_backward_persistent<float4, true> : k_backward_persistent<float4, false>);
     int per_sm = 0;
     if ((rc = status_of(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0))))
         return rc;

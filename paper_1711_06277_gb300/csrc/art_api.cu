@@ -584,6 +584,7 @@ void art_destroy_grid(art_grid* g)
     dev_free(g->d_srcL);
     dev_free(g->d_rec);
     dev_free(g->d_recf);
+    dev_free(g->d_recw);
     dev_free(g->d_chi2);
     dev_free(g->d_srcLn);
     dev_free(g->d_dL_scratch);

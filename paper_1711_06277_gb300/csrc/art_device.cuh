@@ -136,6 +136,7 @@ struct Sched {
 
 // Everything the trace kernels read.
 struct CellF;
+struct CellW;
 
 struct TraceArgs {
     int nx, ny, nz;
@@ -159,6 +160,7 @@ struct TraceArgs {
     float gscale;            // adjoint: sigma_H * dx / dV (gamma per unit G)
     const float* srcL;       // adjoint: source luminosities (gradients scale with them)
     const CellF* recf;       // adjoint with a force term: per cell {chi, chi_H, w, 0}, {v, 0}
+    const CellW* recw;       // adjoint without dust and force term: per cell {chi, w}
     df dmax;                 // d_max cutoff in cell units (kernels built for a cutoff only)
     float fscale;            // adjoint: force per unit momentum (1 / dV)
 };
@@ -190,6 +192,18 @@ struct CellF {
 };
 __device__ __forceinline__ float chi_of(const CellF& c) { return c.a.x; }
 __device__ __forceinline__ CellF load_cell(const CellF* p) { return {__ldg(&p->a), __ldg(&p->b)}; }
+// Cell record of a reverse sweep without dust and without a force term: {chi, w} (8 bytes).
+// Without dust the neutral-H opacity is chi itself (both are float(n_H0 sigma_H dx)).
+struct __align__(8) CellW {
+    float chi, w;
+};
+__device__ __forceinline__ float chi_of(const CellW& c) { return c.chi; }
+__device__ __forceinline__ CellW load_cell(const CellW* p)
+{
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return {v.x, v.y};
+}
+template <> __device__ __forceinline__ CellW cell_zero<CellW>() { return {0.f, 0.f}; }
 template <> __device__ __forceinline__ CellF cell_zero<CellF>()
 {
     return {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};

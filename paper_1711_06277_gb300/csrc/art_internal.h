@@ -77,6 +77,7 @@ struct art_grid {
     float* d_srcL = nullptr;
     float4* d_rec = nullptr;     // per-cell {chi, chi_H, w, 0} of the reverse sweep (padded)
     art::CellF* d_recf = nullptr;  // the same with the force weight (loss with a force term)
+    art::CellW* d_recw = nullptr;  // {chi, w} per cell (loss without dust or force term)
     double* d_dL_scratch = nullptr;
     size_t srcL_cap = 0;
     std::vector<float> h_srcL;
