@@ -33,7 +33,9 @@ from paper_1711_06277_gb300 import synth  # noqa: E402
 
 BYTES_PER_CROSSING = 20  # 4 B opacity gather + 16 B deposit reduction
 
-BYTES_PER_CROSSING_ADJ = 36  # reverse sweep: 16 B record per step of each pass + 4 B reduction
+# reverse sweep, per forward crossing: the cell record gathered in each of the two passes
+# ({chi, w}: 8 B for a loss on gamma without dust) and one 4-byte gradient reduction
+BYTES_PER_CROSSING_ADJ = 2 * 8 + 4
 
 CONFIGS = {
     # name: grid side, log-density spread, sources, seed, mean n_H, sigma_H, alpha_B, x_n(0)
@@ -376,8 +378,9 @@ def _time(fn, stream, reps=3):
 
 
 def adjoint_ratio(A, dev, name="c4_128_16src"):
-    """Forward trace vs hand-written adjoint (loss = sum w gamma), and the adjoint's roofline
-    at 36 algorithmic bytes per forward crossing."""
+    """Forward trace vs hand-written adjoint (loss = sum w gamma, no dust), and the adjoint's
+    roofline at 20 algorithmic bytes per forward crossing (two 8-byte record gathers and a
+    4-byte gradient reduction)."""
     import torch
     cfg = CONFIGS[name]
     nH_h, pos, L = make_workload(cfg)
