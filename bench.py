@@ -172,7 +172,7 @@ def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1711_06277_gb300 import art as A
 
-    dev = torch.device("cuda", local_rank)
+    dev = torch.device("cuda", local_rank % torch.cuda.device_count())
     torch.cuda.set_device(dev)
     cfg = CONFIGS[args.config]
     n = cfg["n"]
@@ -246,7 +246,7 @@ def run_ours(args, rank, world, local_rank):
         except Exception as e:  # report and run eagerly
             graph, graph_note = None, f"capture failed: {type(e).__name__}: {e}"[:200]
     elif sharded is not None:
-        graph_note = "eager: a step holds an NCCL all-reduce"
+        graph_note = "eager: a step holds a collective all-reduce"
 
     def step():
         with torch.cuda.stream(stream):
@@ -264,7 +264,7 @@ def run_ours(args, rank, world, local_rank):
     step_ms = []
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     sev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    with ClockSampler(local_rank) as clk:
+    with ClockSampler(dev.index) as clk:
         ev[0].record(stream)
         for _ in range(args.steps):
             sev[0].record(stream)
@@ -627,8 +627,10 @@ def main():
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local_rank)
-        dist.init_process_group("nccl")
+        torch.cuda.set_device(local_rank % torch.cuda.device_count())
+        # NCCL across the node's GPUs; ART_BENCH_BACKEND=gloo runs the same split path with
+        # host-side collectives (e.g. several ranks sharing one GPU to check the path)
+        dist.init_process_group(os.environ.get("ART_BENCH_BACKEND", "nccl"))
     r = run_ours(args, rank, world, local_rank)
     if rank != 0:
         return
