@@ -2,8 +2,9 @@
 
 Each test compares against something other than the oracle's own formulas: brute-force
 dense sampling of the ray, hand-computed visit sequences, exact geometric exit lengths,
-exact photon bookkeeping, the paper's split radius and ray counts, and the r^-2 vacuum law
-with the accuracy the paper reports.
+exact photon bookkeeping, the paper's split radius and ray counts, the r^-2 vacuum law
+with the accuracy the paper reports, and FP64 quadrature of the exact cell averages in a
+uniform medium.
 """
 import json
 import math
@@ -195,6 +196,46 @@ def test_vacuum_inverse_square_accuracy():
     r16 = O.trace(_prob(n, pos=[[0.5, 0.5, 0.5]], level0=4, m_ray=16.0), nthreads=4)
     err16 = np.abs(r16.energy[sel] / exact - 1)
     assert np.median(err16) < 0.5 * np.median(err4)
+
+
+def _cell_average_uniform(n, chi, c):
+    """(1/dV) * integral over each cell of e^{-chi r} / (4 pi r^2) for a unit source at
+    cell coordinates (c, c, c): composite Gauss-Legendre, 2 sub-intervals x 6 nodes per
+    axis in FP64 (accurate to 1e-9 in every cell but the source's own)."""
+    x, w = np.polynomial.legendre.leggauss(6)
+    nodes = np.concatenate([(s + (x + 1) / 2) / 2 for s in range(2)])
+    wts = np.concatenate([w / 4, w / 4])
+    q = nodes.size
+    d = ((np.arange(n)[:, None] + nodes[None, :]).reshape(-1) - c) / n
+    W = np.tile(wts, n)
+    out = np.zeros((n, n, n))
+    for kz in range(n):
+        dz, wz = d[kz * q:(kz + 1) * q], W[kz * q:(kz + 1) * q]
+        r2 = dz[:, None, None] ** 2 + d[None, :, None] ** 2 + d[None, None, :] ** 2
+        f = np.exp(-chi * np.sqrt(r2)) / (4 * np.pi * r2)
+        f *= wz[:, None, None] * W[None, :, None] * W[None, None, :]
+        out[kz] = f.reshape(q, n, q, n, q).sum(axis=(0, 2, 4))
+    return out
+
+
+def test_uniform_medium_converges_to_exact_cell_average():
+    """In a uniform medium the energy density of every cell (Eq. e:Erad with the segment
+    average of Eq. e:photrate2) tends to the exact cell average of L e^{-chi r}/(4 pi r^2)
+    as the rays per cell m_ray grow (Sec. 2.1), with the error falling about as 1/m_ray."""
+    n, chi, c = 16, 4.0, 8.5                  # 0.25 optical depth per cell, source at a centre
+    exact = _cell_average_uniform(n, chi, c)
+    cc = np.arange(n) + 0.5
+    z, y, x = np.meshgrid(cc, cc, cc, indexing="ij")
+    sel = np.sqrt((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2) > 0.5   # all but the source cell
+    med = []
+    for m in (4.0, 16.0, 64.0, 256.0, 1000.0):
+        r = O.trace(_prob(n, nH0=np.full((n, n, n), chi), pos=[[c / n] * 3], level0=4,
+                          m_ray=m), nthreads=4)
+        med.append(float(np.median(np.abs(r.energy[sel] / exact[sel] - 1))))
+    assert med[0] < 0.1
+    for a, b in zip(med, med[1:]):
+        assert b < 0.5 * a
+    assert med[-1] < 1e-3
 
 
 def test_two_bin_closed_forms():
