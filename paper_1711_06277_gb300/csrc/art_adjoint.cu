@@ -129,7 +129,8 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
     const unsigned b32 = (unsigned)begin, e32 = (unsigned)end;
     unsigned wnext = 0, wend = 0;
     bool more = true;
-    int mode = 0;          // 0 idle, 1 pass 1 (level l), 2 pass 2 (level lv <= l)
+    int mode = 0;          // 0 idle, 1 pass 1 (level l), 2 pass 2 (level lv <= l),
+                           // 3 pass 2 ended, completion pending
     int lv = l;            // level of the ray being walked
     WalkT<Cell> W;
     // pass-1 start of the ray (next face per axis, start cell), so that a leaf's pass 2
@@ -156,7 +157,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
     // dL, the parent's sum, and possibly the parent's pass 2 in this lane.
     auto complete = [&]() {
         for (;;) {
-            dl_add(D, A.dL, __ldcg(A.buf[lv].src + slot), own);
+            dl_add(D, A.dL, s, own);  // every ray of the chain has source s
             if (lv == A.level0) { mode = 0; return; }
             const RayBuf Bl = A.buf[lv];
             const RayBuf Pl = A.buf[lv - 1];
@@ -241,7 +242,7 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
         }
 #pragma unroll 1
         for (int k = 0; k < ART_ADJ_STEPS; ++k) {
-            if (mode != 0) {
+            if (mode == 1 || mode == 2) {
                 const float4 cm = rec_main(W.cell);
                 const float wv = cm.z;   // weight and neutral-H opacity of this cell
                 const float hv = cm.y;
@@ -303,11 +304,16 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
                             mode = 2;
                         }
                     } else {
-                        complete();
+                        mode = 3;
                     }
                 }
             }
         }
+        // Completions of the round's finished pass-2 walks run together: the count-down of
+        // the parent with its memory ordering, and the set-up of the parent's pass 2 for a
+        // last child, whose latencies then overlap across lanes (measured 4 % faster than
+        // completing each walk in its own step, and faster than batches of 1 to 8 lanes).
+        if (mode == 3) complete();
     }
     tally_crossings(T, ncross);
     count_rays(A.stats, l, nrays);
