@@ -434,7 +434,7 @@ def compare_schedules(A, dev):
 def per_config(A, dev):
     """Crossings/s and the trace's roofline fraction (20 B per crossing) on configs 1-4:
     the persistent schedule writing gamma and force, best of 3 after a warm-up trace;
-    config 3 with autotuned launch knobs."""
+    configs 2-4 with autotuned launch knobs (config 1 is bound by its launch latency)."""
     import torch
     peak, _ = _measured_peaks()
     out = {}
@@ -444,7 +444,7 @@ def per_config(A, dev):
         nH_h, pos, L = make_workload(cfg)
         nH0 = torch.from_numpy(nH_h).to(dev)
         p = _params(A, cfg)
-        if name == "c3_256_64src":
+        if name != "c1_32_uniform":
             from paper_1711_06277_gb300 import autotune
             p = autotune.tune(nH0, 1.0 / cfg["n"], pos, L, p)
         g = A.Grid(nH0, 1.0 / cfg["n"], stream=stream)
@@ -457,7 +457,9 @@ def per_config(A, dev):
         g.close()
         rate = st["crossings"] / (ms / 1e3)
         out[name] = {"crossings": st["crossings"], "ms": ms, "crossings_per_s": rate,
-                     "roofline_frac": rate * BYTES_PER_CROSSING / 1e9 / peak}
+                     "roofline_frac": rate * BYTES_PER_CROSSING / 1e9 / peak,
+                     "knobs": {"chunk": p.chunk, "block_threads": p.block_threads,
+                               "queue_capacity": p.queue_capacity}}
     return out
 
 
