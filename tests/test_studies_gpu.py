@@ -121,3 +121,15 @@ def test_rtype_front_resolutions(art):
         assert abs(r128[t] / r64[t] - 1) < 0.02, (t, r64[t], r128[t])
         assert abs(r128[t] / _rtype_exact(t) - 1) < (0.06 if t < 4 else 0.03), (t, r128[t], steps)
     assert abs(r128[8.0] / _rtype_exact(8.0) - 1) < 0.015
+
+
+def test_rtype_front_256(art):
+    """Sec. 3.3.1 at the top of the paper's range of resolutions (64^3 to 256^3): the 256^3
+    front agrees with the 128^3 one within 2 % at every checkpoint and with Eq. e:Rtype
+    within about 1 % at 8 t_rec."""
+    r128, _ = _rtype_cached(art, 128)
+    r256, steps = _rtype_cached(art, 256)
+    for t in r128:
+        assert abs(r256[t] / r128[t] - 1) < 0.02, (t, r128[t], r256[t])
+        assert abs(r256[t] / _rtype_exact(t) - 1) < (0.06 if t < 4 else 0.03), (t, r256[t], steps)
+    assert abs(r256[8.0] / _rtype_exact(8.0) - 1) < 0.015
