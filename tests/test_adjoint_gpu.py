@@ -273,3 +273,29 @@ def test_autograd_with_dust(art):
     out = g.trace(p, force=False)
     PA.compare_field(out["gamma"].cpu().numpy(), ref.gamma, what="gamma after backward")
     g.close()
+
+
+def test_adjoint_config5_512_8src(art):
+    """The reverse sweep at full size: the 512^3 workload the bench times the adjoint on
+    (lognormal sigma_ln = 2, n_H = 100 rho, x_n = 1e-3, sigma_H = 0.1, loss = sum w gamma, all
+    8 of its sources), in the launch configuration the bench uses, against the oracle's
+    reverse sweep."""
+    import os
+    n = 512
+    rho = synth.lognormal_field(n, 2.0, seed=5)
+    nH0 = (1e-3 * (100.0 * rho).astype(np.float32)).astype(np.float32)
+    pos = synth.uniform_positions(8, seed=5)
+    L = synth.power_law_luminosities(8, seed=5)
+    w = synth.uniform_weights(n, seed=5).astype(np.float32)
+    p = art.Params(level0=4, m_ray=4.0, tau_max=30.0, sigma_H=0.1)
+    dev = torch.device("cuda")
+    g = art.Grid(torch.from_numpy(nH0).to(dev), 1.0 / n)
+    g.add_sources(pos, L)
+    fwd = g.trace(p, force=False)
+    grad, dL, st = g.trace_backward(p, torch.from_numpy(w).to(dev))
+    out = dict(grad=grad.cpu().numpy(), dL=dL.cpu().numpy(), stats=st, fstats=fwd["stats"],
+               loss=float((w.astype(np.float64) * fwd["gamma"].cpu().numpy()).sum()))
+    g.close()
+    prob = O.Problem(nH0=nH0, pos=pos, L=L, dx=1.0 / n, sigma_H=0.1, level0=4, tau_max=30.0)
+    ref = O.trace_adjoint(prob, w, nthreads=os.cpu_count() or 8)
+    _check(out, ref, L)
