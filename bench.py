@@ -58,12 +58,16 @@ CONFIGS = {
 
 
 def kernel_sources_digest() -> str:
-    """SHA-256 over the CUDA sources, to tell whether a stored ncu capture still applies."""
+    """SHA-256 over the sources the forward trace kernel is compiled from (its translation
+    unit art_api.cu and every header), to tell whether a stored ncu capture of it still
+    applies; the reverse sweep, x_n and work-estimate units do not enter."""
     import glob
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1711_06277_gb300", "csrc")
-    for path in sorted(glob.glob(os.path.join(csrc, "*.cu*")) + glob.glob(os.path.join(csrc, "*.h"))):
+    files = [os.path.join(csrc, "art_api.cu")] + glob.glob(os.path.join(csrc, "*.cuh")) \
+        + glob.glob(os.path.join(csrc, "*.h")) + [os.path.join(ROOT, "include", "art.h")]
+    for path in sorted(files):
         with open(path, "rb") as f:
             h.update(os.path.basename(path).encode() + b"\0" + f.read())
     return h.hexdigest()

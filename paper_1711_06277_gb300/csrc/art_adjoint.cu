@@ -90,13 +90,15 @@ template <> __device__ __forceinline__ const float4* recs_of<float4>(const Trace
 template <> __device__ __forceinline__ const CellF* recs_of<CellF>(const TraceArgs& A) { return A.recf; }
 template <> __device__ __forceinline__ const CellW* recs_of<CellW>(const TraceArgs& A) { return A.recw; }
 
-// Idle lanes of a warp before it refills them from the queue, and steps between refill
-// checks (measured on the 128^3 / 16-source case).
+// Idle lanes of a warp before it refills them from the queue, and steps per round (between
+// refill checks; completions run at the end of each round). Measured on the 128^3 /
+// 16-source and 512^3 / 8-source cases: 32 steps at 16 lanes beat 8 at 12 by 1 % and 10 %;
+// longer rounds or a threshold of 20 lanes gain a little more at 512^3 and lose at 128^3.
 #ifndef ART_ADJ_IDLE
-#define ART_ADJ_IDLE 12
+#define ART_ADJ_IDLE 16
 #endif
 #ifndef ART_ADJ_STEPS
-#define ART_ADJ_STEPS 8
+#define ART_ADJ_STEPS 32
 #endif
 
 // One expand phase of the reverse sweep on the rays in slots [cursor .. end) of level l
@@ -312,7 +314,8 @@ __device__ void run_adjoint(const TraceArgs& A, int l, unsigned long long* curso
         // Completions of the round's finished pass-2 walks run together: the count-down of
         // the parent with its memory ordering, and the set-up of the parent's pass 2 for a
         // last child, whose latencies then overlap across lanes (measured 4 % faster than
-        // completing each walk in its own step, and faster than batches of 1 to 8 lanes).
+        // completing each walk in its own step, and faster than batches of 1 to 8 lanes, in
+        // rounds of 8 steps).
         if (mode == 3) complete();
     }
     tally_crossings(T, ncross);
