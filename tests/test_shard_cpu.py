@@ -55,6 +55,9 @@ def test_partition_large_balance_and_determinism():
     # one rank takes everything; an empty source list is valid
     assert shard.partition(work[:5], 1)[0].tolist() == [0] * 5
     assert len(shard.partition([], 3)[0]) == 0
+    # more ranks than sources: each source alone on a rank, the other ranks empty
+    rank, load = shard.partition([3.0, 1.0], 4)
+    assert sorted(rank.tolist()) == [0, 1] and sorted(load.tolist()) == [0.0, 0.0, 1.0, 3.0]
 
 
 def test_partition_rejects_bad_input():
