@@ -105,8 +105,9 @@ template <> __device__ __forceinline__ const CellW* recs_of<CellW>(const TraceAr
 // (phase starting at slot `begin`). Pass 1 walks each ray for its own weighted sum. A ray
 // that splits stores that sum, a pending-children count of 4 and its children (in order, as
 // in the forward trace). A ray that ends without splitting (a leaf) walks again at once
-// (pass 2) from the start state kept from pass 1, depositing its gradients; it then adds
-// its total to its parent and counts the parent down. The lane that brings a parent's
+// (pass 2) from the start state kept from pass 1, depositing its gradients; once the warp's
+// round of steps ends it adds its total to its parent and counts the parent down (the
+// completions of a round run together). The lane that brings a parent's
 // count to zero takes over the parent's pass 2 (its level below this phase's), and so on
 // towards the base level: no separate collapse phase is needed, because the deepest-first
 // schedule does not reuse a level's slots before everything below it has finished. The
